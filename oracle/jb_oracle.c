@@ -1,0 +1,1197 @@
+/*
+ * FP64 CPU oracle -- TEST INFRASTRUCTURE ONLY (see jb_oracle.h).
+ *
+ * A plain sequential statement of one time step of the paper's rigid-body
+ * engine, written in the paper's order:
+ *   Sec. 4.2  external forces and semi-implicit Euler (Eq. newton_euler),
+ *   Sec. 6.1  AABB broadphase (Eq. aabb),
+ *   Sec. 6.2  OBB separating-axis test over 15 axes,
+ *   Sec. 6.2.1 contact manifold by Sutherland-Hodgman face clipping,
+ *   Sec. 7.1  Jacobian / effective mass (Eq. keff), normal impulse (Eq. lambda_n),
+ *   Sec. 7.2  box Coulomb friction (Eq. coulomb_pgs),
+ *   Sec. 7.3  sequential Projected Gauss-Seidel (Listing "PGS core"),
+ *   Sec. 4.1  quaternion integration (Eq. quat_int),
+ *   Sec. 7.4  Baumgarte position correction (Eq. baumgarte),
+ *   Sec. 8    support polygon margin (Eq. stability), collapse (Eq. collapse),
+ *             rest test (Sec. 8.3).
+ * Where the paper is silent or garbled, the reading taken is stated at the
+ * point of use ("reading:").  Gauss-Seidel runs in natural order: ground pairs
+ * by body, then pairs (i, j) ascending, points in manifold order, rows n, t1, t2.
+ */
+#include "jb_oracle.h"
+
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define MAXP 4          /* contact points per pair (Sec. 6.2.1 step d) */
+#define TIE_ABS 1e-7    /* reading: SAT axis hysteresis (m) */
+#define EDGE_REL 0.05   /* reading: cross axis must beat the face axis by 5% */
+#define CROSS_EPS 1e-6  /* reading: skip degenerate cross axes */
+#define INC_TIE 1e-9    /* reading: incident-face choice hysteresis */
+#define OR_PI 3.14159265358979323846
+
+typedef struct {
+  double x[3], q[4], v[3], w[3];
+  double half[3];
+  double mass, invm, invI[3], mu;
+  int active, is_static;
+  double R[3][3], Iw[3][3];     /* rotation, world inverse inertia (per substep) */
+  double x0[3], z0[3];          /* initial position and thickness axis */
+  double f[3];                  /* external force */
+  int f_steps;
+} or_body;
+
+typedef struct {
+  int a, b;                     /* episode-local; a = -1 is the ground */
+  int axis, ref_face, inc_face, np;
+  double n[3], t1[3], t2[3];
+  double delta, depth_max, mu;
+  double p[MAXP][3], depth[MAXP], local[MAXP][3];
+  double rA[MAXP][3], rB[MAXP][3];
+  double k[MAXP][3];            /* inverse effective mass of rows n, t1, t2 */
+  double bias[MAXP];
+  double lam[MAXP][3];
+} or_pair;
+
+typedef struct {
+  int nb;
+  or_body* b;
+  or_body ground;               /* static, zero velocity, identity frame */
+  double ground_mu;
+  or_pair *pairs, *prev;
+  int np, cap, nprev, capprev;
+  /* schedule */
+  int n_moves, mi, phase, remaining, pb, rest_left;
+  const int *mv_block, *mv_axis, *mv_remove, *mv_push, *mv_settle;
+  const double *mv_sign, *mv_factor, *mv_k;
+  /* statistics */
+  int status, collapsed, resting, last_sweeps;
+  long steps, total_sweeps, solves;
+  double body_steps, last_res, max_res, ek;
+} or_episode;
+
+struct or_world {
+  int E, B;
+  int* body_off;
+  or_episode* ep;
+  or_params P;
+  /* schedule storage */
+  int *m_block, *m_axis, *m_remove, *m_push, *m_settle;
+  double *m_sign, *m_factor, *m_k;
+};
+
+/* ------------------------------------------------------------------ vectors */
+static double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static void cross3(const double* a, const double* b, double* c) {
+  double t0 = a[1] * b[2] - a[2] * b[1], t1 = a[2] * b[0] - a[0] * b[2], t2 = a[0] * b[1] - a[1] * b[0];
+  c[0] = t0; c[1] = t1; c[2] = t2;
+}
+static double norm3(const double* a) { return sqrt(dot3(a, a)); }
+static void axpy3(double s, const double* x, double* y) { y[0] += s * x[0]; y[1] += s * x[1]; y[2] += s * x[2]; }
+static void matvec3(const double M[3][3], const double* x, double* y) {
+  double t[3];
+  for (int i = 0; i < 3; ++i) t[i] = M[i][0] * x[0] + M[i][1] * x[1] + M[i][2] * x[2];
+  y[0] = t[0]; y[1] = t[1]; y[2] = t[2];
+}
+static void col3(const double R[3][3], int k, double* c) { c[0] = R[0][k]; c[1] = R[1][k]; c[2] = R[2][k]; }
+static double sgn(double v) { return v >= 0.0 ? 1.0 : -1.0; }
+static double clampd(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/* ------------------------------------------------- Sec. 4.1 rotation, inertia */
+/* Eq. rotmat: rotation matrix of the unit quaternion q = [w, x, y, z]. */
+static void rotmat(const double* q, double R[3][3]) {
+  double w = q[0], x = q[1], y = q[2], z = q[3];
+  R[0][0] = 1 - 2 * (y * y + z * z); R[0][1] = 2 * (x * y - z * w);     R[0][2] = 2 * (x * z + y * w);
+  R[1][0] = 2 * (x * y + z * w);     R[1][1] = 1 - 2 * (x * x + z * z); R[1][2] = 2 * (y * z - x * w);
+  R[2][0] = 2 * (x * z - y * w);     R[2][1] = 2 * (y * z + x * w);     R[2][2] = 1 - 2 * (x * x + y * y);
+}
+void or_rotmat(const double* q, double* R) { rotmat(q, (double(*)[3])R); }
+
+/* Eq. inertia: I_body = m/12 diag(w^2+h^2, l^2+h^2, l^2+w^2), l, w, h = full
+   dimensions along body x, y, z. */
+void or_body_inertia(double m, const double* half, double* I) {
+  double l = 2 * half[0], w = 2 * half[1], h = 2 * half[2];
+  I[0] = m / 12.0 * (w * w + h * h);
+  I[1] = m / 12.0 * (l * l + h * h);
+  I[2] = m / 12.0 * (l * l + w * w);
+}
+
+/* Sec. 4.1.2: I_world^-1 = R I_body^-1 R^T. */
+static void update_frame(or_body* B) {
+  rotmat(B->q, B->R);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0;
+      for (int k = 0; k < 3; ++k) s += B->R[i][k] * B->invI[k] * B->R[j][k];
+      B->Iw[i][j] = s;
+    }
+}
+
+/* --------------------------------------------------------- Sec. 6.2 SAT ----- */
+typedef struct { double x[3]; double R[3][3]; double h[3]; } box_t;
+
+/* Projected radius of a box on unit axis u: r = sum_i h_i |a_i . u|. */
+static double proj_radius(const box_t* b, const double* u) {
+  double r = 0, a[3];
+  for (int i = 0; i < 3; ++i) { col3(b->R, i, a); r += b->h[i] * fabs(dot3(a, u)); }
+  return r;
+}
+
+/* All 15 axes: A0..A2, B0..B2, then A_i x B_j (i-major).  delta = rA + rB - |d.u|.
+   Reading: cross axes with |A_i x B_j| < 1e-6 are skipped (parallel edges). */
+static void sat15(const box_t* A, const box_t* B, double delta[15], int valid[15], double U[15][3]) {
+  double d[3] = {B->x[0] - A->x[0], B->x[1] - A->x[1], B->x[2] - A->x[2]};
+  for (int k = 0; k < 15; ++k) {
+    double u[3];
+    if (k < 3) col3(A->R, k, u);
+    else if (k < 6) col3(B->R, k - 3, u);
+    else {
+      double a[3], b[3];
+      col3(A->R, (k - 6) / 3, a); col3(B->R, (k - 6) % 3, b);
+      cross3(a, b, u);
+      double l = norm3(u);
+      if (l < CROSS_EPS) { valid[k] = 0; delta[k] = 0; U[k][0] = U[k][1] = U[k][2] = 0; continue; }
+      u[0] /= l; u[1] /= l; u[2] /= l;
+    }
+    valid[k] = 1;
+    U[k][0] = u[0]; U[k][1] = u[1]; U[k][2] = u[2];
+    delta[k] = proj_radius(A, u) + proj_radius(B, u) - fabs(dot3(d, u));
+  }
+}
+
+/* Axis choice.  Reading (the paper only says "the axis with minimum delta"):
+   face axes in order A0..B2, a later one replaces the current best only if
+   smaller by 1e-7 m; likewise among cross axes; a cross axis wins only if
+   delta_edge < delta_face - (0.05 |delta_face| + 1e-7).  Contact exists iff the
+   minimum delta over all valid axes exceeds -margin (speculative contacts). */
+static int sat_select(const double delta[15], const int valid[15], double* dmin_out) {
+  double dmin = delta[0];
+  for (int k = 1; k < 15; ++k) if (valid[k] && delta[k] < dmin) dmin = delta[k];
+  *dmin_out = dmin;
+  int bf = 0;
+  for (int k = 1; k < 6; ++k) if (delta[k] < delta[bf] - TIE_ABS) bf = k;
+  int be = -1;
+  for (int k = 6; k < 15; ++k)
+    if (valid[k] && (be < 0 || delta[k] < delta[be] - TIE_ABS)) be = k;
+  if (be >= 0 && delta[be] < delta[bf] - (EDGE_REL * fabs(delta[bf]) + TIE_ABS)) return be;
+  return bf;
+}
+
+/* ------------------------------------------------- Sec. 6.2.1 manifold ----- */
+typedef struct { int n; double p[8][3]; } poly_t;
+
+/* Sutherland-Hodgman: keep the part of the polygon with (p - c).u <= h. */
+static void clip_plane(const poly_t* in, poly_t* out, const double* c, const double* u, double h) {
+  out->n = 0;
+  if (in->n == 0) return;
+  for (int i = 0; i < in->n; ++i) {
+    const double* S = in->p[(i + in->n - 1) % in->n];
+    const double* E = in->p[i];
+    double dS = (S[0] - c[0]) * u[0] + (S[1] - c[1]) * u[1] + (S[2] - c[2]) * u[2] - h;
+    double dE = (E[0] - c[0]) * u[0] + (E[1] - c[1]) * u[1] + (E[2] - c[2]) * u[2] - h;
+    if (dE <= 0) {
+      if (dS > 0 && out->n < 8) {
+        double t = dS / (dS - dE);
+        for (int j = 0; j < 3; ++j) out->p[out->n][j] = S[j] + t * (E[j] - S[j]);
+        out->n++;
+      }
+      if (out->n < 8) { memcpy(out->p[out->n], E, sizeof(double) * 3); out->n++; }
+    } else if (dS <= 0 && out->n < 8) {
+      double t = dS / (dS - dE);
+      for (int j = 0; j < 3; ++j) out->p[out->n][j] = S[j] + t * (E[j] - S[j]);
+      out->n++;
+    }
+  }
+}
+
+/* Area of the convex hull of 4 coplanar-ish points measured across n. */
+static double tri_area(const double* a, const double* b, const double* c, const double* n) {
+  double u[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, v[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]}, w[3];
+  cross3(u, v, w);
+  return 0.5 * fabs(dot3(w, n));
+}
+static double quad_area(const double* a, const double* b, const double* c, const double* d, const double* n) {
+  const double* P[4] = {a, b, c, d};
+  double s[3] = {0, 0, 0}, t[3];
+  for (int i = 0; i < 4; ++i) { cross3(P[i], P[(i + 1) % 4], t); axpy3(1.0, t, s); }
+  return 0.5 * fabs(dot3(s, n));
+}
+static double hull4_area(const double* a, const double* b, const double* c, const double* d, const double* n) {
+  double m = quad_area(a, b, c, d, n), t;
+  if ((t = quad_area(a, b, d, c, n)) > m) m = t;
+  if ((t = quad_area(a, c, b, d, n)) > m) m = t;
+  if ((t = tri_area(a, b, c, n)) > m) m = t;
+  if ((t = tri_area(a, b, d, n)) > m) m = t;
+  if ((t = tri_area(a, c, d, n)) > m) m = t;
+  if ((t = tri_area(b, c, d, n)) > m) m = t;
+  return m;
+}
+
+/* Reading of "sample up to 4 points": (1) deepest, (2) farthest from (1),
+   (3) largest triangle with (1),(2), (4) largest added hull area; lowest index
+   wins ties; output in that order.  Applied only when more than 4 remain. */
+static int reduce4(int n, double P[][3], double* D, const double* nrm, int* sel) {
+  if (n <= 4) { for (int i = 0; i < n; ++i) sel[i] = i; return n; }
+  int used[8] = {0};
+  int i1 = 0;
+  for (int i = 1; i < n; ++i) if (D[i] > D[i1]) i1 = i;
+  used[i1] = 1;
+  int i2 = -1; double best = -1;
+  for (int i = 0; i < n; ++i) {
+    if (used[i]) continue;
+    double d[3] = {P[i][0] - P[i1][0], P[i][1] - P[i1][1], P[i][2] - P[i1][2]};
+    double s = dot3(d, d);
+    if (s > best) { best = s; i2 = i; }
+  }
+  used[i2] = 1;
+  int i3 = -1; best = -1;
+  for (int i = 0; i < n; ++i) {
+    if (used[i]) continue;
+    double s = tri_area(P[i1], P[i2], P[i], nrm);
+    if (s > best) { best = s; i3 = i; }
+  }
+  used[i3] = 1;
+  double base = tri_area(P[i1], P[i2], P[i3], nrm);
+  int i4 = -1; best = -1;
+  for (int i = 0; i < n; ++i) {
+    if (used[i]) continue;
+    double s = hull4_area(P[i1], P[i2], P[i3], P[i], nrm) - base;
+    if (s > best) { best = s; i4 = i; }
+  }
+  sel[0] = i1; sel[1] = i2; sel[2] = i3; sel[3] = i4;
+  return 4;
+}
+
+/* Reading of the tangent basis: t1 = normalize(e - (e.n) n) with e = world X,
+   or world Y when |n.X| > 0.9; t2 = n x t1. */
+static void tangent_basis(const double* n, double* t1, double* t2) {
+  double e[3] = {1, 0, 0};
+  if (fabs(n[0]) > 0.9) { e[0] = 0; e[1] = 1; }
+  double en = dot3(e, n);
+  double t[3] = {e[0] - en * n[0], e[1] - en * n[1], e[2] - en * n[2]};
+  double l = norm3(t);
+  t1[0] = t[0] / l; t1[1] = t[1] / l; t1[2] = t[2] / l;
+  cross3(n, t1, t2);
+}
+
+/* Points are written to pr->p / depth; returns the count kept. */
+static int finish_points(or_pair* pr, int n, double P[][3], double* D, const double* nrm) {
+  int sel[4];
+  int m = reduce4(n, P, D, nrm, sel);
+  double dm = -1e300;
+  for (int i = 0; i < m; ++i) {
+    memcpy(pr->p[i], P[sel[i]], sizeof(double) * 3);
+    pr->depth[i] = D[sel[i]];
+    if (D[sel[i]] > dm) dm = D[sel[i]];
+  }
+  pr->np = m;
+  pr->depth_max = dm;
+  return m;
+}
+
+/* Face-face manifold.  Reading of steps a-d: the reference face is the face of
+   the SAT-axis owner whose outward normal is along the contact direction, the
+   incident face is the other box's face most anti-parallel to it; the incident
+   quad is clipped by the reference face's four side planes; per-point depth is
+   the distance below the reference face; points with depth > -margin are kept;
+   the contact point is the midpoint between the incident point and the face. */
+static int face_manifold(const box_t* A, const box_t* B, int axis, const double* n, double margin, or_pair* pr) {
+  const box_t *ref, *inc;
+  int ra;
+  double nref[3];
+  if (axis < 3) { ref = A; inc = B; ra = axis; nref[0] = n[0]; nref[1] = n[1]; nref[2] = n[2]; }
+  else { ref = B; inc = A; ra = axis - 3; nref[0] = -n[0]; nref[1] = -n[1]; nref[2] = -n[2]; }
+  double ax[3];
+  col3(ref->R, ra, ax);
+  double sr = sgn(dot3(ax, nref));
+  double cr[3] = {ref->x[0] + sr * ref->h[ra] * ax[0], ref->x[1] + sr * ref->h[ra] * ax[1],
+                  ref->x[2] + sr * ref->h[ra] * ax[2]};
+  int r1 = (ra + 1) % 3, r2 = (ra + 2) % 3;
+  double u1[3], u2[3];
+  col3(ref->R, r1, u1); col3(ref->R, r2, u2);
+  /* incident face */
+  int ji = 0; double bestd = -1;
+  for (int j = 0; j < 3; ++j) {
+    double c[3]; col3(inc->R, j, c);
+    double dd = fabs(dot3(c, nref));
+    if (dd > bestd + INC_TIE) { bestd = dd; ji = j; }
+  }
+  double bj[3]; col3(inc->R, ji, bj);
+  double si = -sgn(dot3(bj, nref));
+  double ci[3] = {inc->x[0] + si * inc->h[ji] * bj[0], inc->x[1] + si * inc->h[ji] * bj[1],
+                  inc->x[2] + si * inc->h[ji] * bj[2]};
+  int j1 = (ji + 1) % 3, j2 = (ji + 2) % 3;
+  double v1[3], v2[3];
+  col3(inc->R, j1, v1); col3(inc->R, j2, v2);
+  const double s1[4] = {1, -1, -1, 1}, s2[4] = {1, 1, -1, -1};
+  poly_t a, b;
+  a.n = 4;
+  for (int i = 0; i < 4; ++i)
+    for (int k = 0; k < 3; ++k)
+      a.p[i][k] = ci[k] + s1[i] * inc->h[j1] * v1[k] + s2[i] * inc->h[j2] * v2[k];
+  double mu1[3] = {-u1[0], -u1[1], -u1[2]}, mu2[3] = {-u2[0], -u2[1], -u2[2]};
+  clip_plane(&a, &b, cr, u1, ref->h[r1]);
+  clip_plane(&b, &a, cr, mu1, ref->h[r1]);
+  clip_plane(&a, &b, cr, u2, ref->h[r2]);
+  clip_plane(&b, &a, cr, mu2, ref->h[r2]);
+  double P[8][3], D[8];
+  int m = 0;
+  for (int i = 0; i < a.n; ++i) {
+    double rel[3] = {cr[0] - a.p[i][0], cr[1] - a.p[i][1], cr[2] - a.p[i][2]};
+    double dep = dot3(rel, nref);
+    if (dep > -margin) {
+      for (int k = 0; k < 3; ++k) P[m][k] = a.p[i][k] + 0.5 * dep * nref[k];
+      D[m] = dep;
+      ++m;
+    }
+  }
+  pr->ref_face = 2 * ra + (sr > 0 ? 0 : 1) + (axis < 3 ? 0 : 8);
+  pr->inc_face = 2 * ji + (si > 0 ? 0 : 1);
+  return finish_points(pr, m, P, D, n);
+}
+
+/* Reading for edge-edge contacts (the paper is silent): one point at the
+   midpoint of the closest points of the two supporting edges, depth = delta. */
+static int edge_manifold(const box_t* A, const box_t* B, int axis, const double* n, double delta, or_pair* pr) {
+  int i = (axis - 6) / 3, j = (axis - 6) % 3;
+  double pa[3] = {A->x[0], A->x[1], A->x[2]}, pb[3] = {B->x[0], B->x[1], B->x[2]};
+  for (int m = 0; m < 3; ++m) {
+    double c[3];
+    if (m != i) { col3(A->R, m, c); axpy3(sgn(dot3(c, n)) * A->h[m], c, pa); }
+    if (m != j) { col3(B->R, m, c); axpy3(-sgn(dot3(c, n)) * B->h[m], c, pb); }
+  }
+  double ea[3], eb[3];
+  col3(A->R, i, ea); col3(B->R, j, eb);
+  double r[3] = {pa[0] - pb[0], pa[1] - pb[1], pa[2] - pb[2]};
+  double bb = dot3(ea, eb), c = dot3(ea, r), f = dot3(eb, r);
+  double den = 1.0 - bb * bb;
+  double s = den > 1e-12 ? (bb * f - c) / den : 0.0;
+  s = clampd(s, -A->h[i], A->h[i]);
+  double t = clampd(f + s * bb, -B->h[j], B->h[j]);
+  double P[1][3], D[1] = {delta};
+  for (int k = 0; k < 3; ++k) P[0][k] = 0.5 * ((pa[k] + s * ea[k]) + (pb[k] + t * eb[k]));
+  pr->ref_face = 16 + i;
+  pr->inc_face = 16 + j;
+  return finish_points(pr, 1, P, D, n);
+}
+
+/* Box-box narrowphase; returns 1 and fills axis, n, delta, points if in contact. */
+static int box_pair(const box_t* A, const box_t* B, double margin, or_pair* pr, double* dmin_out) {
+  double delta[15], U[15][3];
+  int valid[15];
+  sat15(A, B, delta, valid, U);
+  double dmin;
+  int ax = sat_select(delta, valid, &dmin);
+  if (dmin_out) *dmin_out = dmin;
+  if (!(dmin > -margin)) return 0;
+  double d[3] = {B->x[0] - A->x[0], B->x[1] - A->x[1], B->x[2] - A->x[2]};
+  double n[3] = {U[ax][0], U[ax][1], U[ax][2]};
+  if (dot3(n, d) < 0) { n[0] = -n[0]; n[1] = -n[1]; n[2] = -n[2]; }
+  pr->axis = ax;
+  pr->delta = delta[ax];
+  memcpy(pr->n, n, sizeof n);
+  int m = ax < 6 ? face_manifold(A, B, ax, n, margin, pr) : edge_manifold(A, B, ax, n, delta[ax], pr);
+  return m > 0;
+}
+
+/* Reading for ground contacts: the ground z = 0 is body A with n = +z; the
+   box corners with z < margin are candidates (depth = -z), reduced to 4. */
+static int ground_pair(const box_t* B, double margin, or_pair* pr) {
+  double P[8][3], D[8];
+  int m = 0;
+  for (int c = 0; c < 8; ++c) {
+    double s0 = (c & 1) ? 1 : -1, s1 = (c & 2) ? 1 : -1, s2 = (c & 4) ? 1 : -1;
+    double p[3];
+    for (int k = 0; k < 3; ++k)
+      p[k] = B->x[k] + s0 * B->h[0] * B->R[k][0] + s1 * B->h[1] * B->R[k][1] + s2 * B->h[2] * B->R[k][2];
+    if (p[2] < margin) {
+      D[m] = -p[2];
+      P[m][0] = p[0]; P[m][1] = p[1]; P[m][2] = p[2] + 0.5 * D[m];
+      ++m;
+    }
+  }
+  if (m == 0) return 0;
+  double n[3] = {0, 0, 1};
+  memcpy(pr->n, n, sizeof n);
+  pr->axis = 15;
+  pr->ref_face = 0;
+  pr->inc_face = 0;
+  finish_points(pr, m, P, D, n);
+  pr->delta = pr->depth_max;
+  return 1;
+}
+
+static void box_of(const or_body* b, box_t* out) {
+  memcpy(out->x, b->x, sizeof out->x);
+  memcpy(out->R, b->R, sizeof out->R);
+  memcpy(out->h, b->half, sizeof out->h);
+}
+
+/* -------------------------------------------------------------- episode ---- */
+static or_body* body_ref(or_episode* E, int i) { return i < 0 ? &E->ground : &E->b[i]; }
+
+static void push_pair(or_episode* E, const or_pair* p) {
+  if (E->np == E->cap) {
+    E->cap = E->cap ? 2 * E->cap : 64;
+    E->pairs = (or_pair*)realloc(E->pairs, sizeof(or_pair) * E->cap);
+  }
+  E->pairs[E->np++] = *p;
+}
+
+/* Sec. 6.1 Eq. aabb broadphase + Sec. 6.2 narrowphase, natural pair order. */
+static void detect(or_episode* E, const or_params* P) {
+  E->np = 0;
+  double ext[E->nb > 0 ? E->nb : 1][3];
+  for (int i = 0; i < E->nb; ++i)
+    for (int k = 0; k < 3; ++k)
+      ext[i][k] = fabs(E->b[i].R[k][0]) * E->b[i].half[0] + fabs(E->b[i].R[k][1]) * E->b[i].half[1] +
+                  fabs(E->b[i].R[k][2]) * E->b[i].half[2];
+  or_pair pr;
+  /* ground pairs first (ground = body -1) */
+  for (int j = 0; j < E->nb; ++j) {
+    or_body* B = &E->b[j];
+    if (!B->active || B->is_static) continue;
+    if (B->x[2] - ext[j][2] > P->aabb_eps) continue;
+    box_t bx; box_of(B, &bx);
+    memset(&pr, 0, sizeof pr);
+    if (ground_pair(&bx, P->contact_margin, &pr)) {
+      pr.a = -1; pr.b = j;
+      pr.mu = fmin(E->ground_mu, B->mu);
+      push_pair(E, &pr);
+    }
+  }
+  for (int i = 0; i < E->nb; ++i) {
+    or_body* A = &E->b[i];
+    if (!A->active) continue;
+    for (int j = i + 1; j < E->nb; ++j) {
+      or_body* B = &E->b[j];
+      if (!B->active || (A->is_static && B->is_static)) continue;
+      int ov = 1;
+      for (int k = 0; k < 3; ++k)
+        if (fabs(A->x[k] - B->x[k]) > ext[i][k] + ext[j][k] + P->aabb_eps) ov = 0;
+      if (!ov) continue;
+      box_t ba, bb; box_of(A, &ba); box_of(B, &bb);
+      memset(&pr, 0, sizeof pr);
+      if (box_pair(&ba, &bb, P->contact_margin, &pr, NULL)) {
+        pr.a = i; pr.b = j;
+        pr.mu = fmin(A->mu, B->mu);
+        push_pair(E, &pr);
+      }
+    }
+  }
+}
+
+/* Sec. 7.1 Eq. keff (read as the inverse effective mass) for each row, the
+   speculative bias, the tangent basis, and A-local point coordinates. */
+static void setup(or_episode* E, double h) {
+  for (int c = 0; c < E->np; ++c) {
+    or_pair* pr = &E->pairs[c];
+    or_body *A = body_ref(E, pr->a), *B = body_ref(E, pr->b);
+    tangent_basis(pr->n, pr->t1, pr->t2);
+    const double* dirs[3] = {pr->n, pr->t1, pr->t2};
+    for (int i = 0; i < pr->np; ++i) {
+      for (int k = 0; k < 3; ++k) { pr->rA[i][k] = pr->p[i][k] - A->x[k]; pr->rB[i][k] = pr->p[i][k] - B->x[k]; }
+      /* local = R_A^T (p - x_A) */
+      for (int k = 0; k < 3; ++k)
+        pr->local[i][k] = A->R[0][k] * pr->rA[i][0] + A->R[1][k] * pr->rA[i][1] + A->R[2][k] * pr->rA[i][2];
+      for (int r = 0; r < 3; ++r) {
+        double ca[3], cb[3], ia[3], ib[3];
+        cross3(pr->rA[i], dirs[r], ca); cross3(pr->rB[i], dirs[r], cb);
+        matvec3(A->Iw, ca, ia); matvec3(B->Iw, cb, ib);
+        pr->k[i][r] = A->invm + B->invm + dot3(ca, ia) + dot3(cb, ib);
+      }
+      /* reading: separated points (depth < 0) may close the gap within the step */
+      pr->bias[i] = pr->depth[i] < 0 ? -pr->depth[i] / h : 0.0;
+      pr->lam[i][0] = pr->lam[i][1] = pr->lam[i][2] = 0;
+    }
+  }
+}
+
+static int pair_key_cmp(int a1, int b1, int a2, int b2) {
+  if (a1 != a2) return a1 < a2 ? -1 : 1;
+  if (b1 != b2) return b1 < b2 ? -1 : 1;
+  return 0;
+}
+
+/* Reading of the warm start: key (a, b, reference face, incident face); a new
+   point inherits the impulse of the nearest old point of the same key within
+   match_radius in body-A local coordinates. */
+static void warm_start_match(or_episode* E, const or_params* P) {
+  if (P->warm_start != 1) return;
+  for (int c = 0; c < E->np; ++c) {
+    or_pair* pr = &E->pairs[c];
+    int lo = 0, hi = E->nprev - 1, found = -1;
+    while (lo <= hi) {
+      int mid = (lo + hi) / 2;
+      int s = pair_key_cmp(E->prev[mid].a, E->prev[mid].b, pr->a, pr->b);
+      if (s == 0) { found = mid; break; }
+      if (s < 0) lo = mid + 1; else hi = mid - 1;
+    }
+    if (found < 0) continue;
+    const or_pair* op = &E->prev[found];
+    if (op->ref_face != pr->ref_face || op->inc_face != pr->inc_face) continue;
+    for (int i = 0; i < pr->np; ++i) {
+      int best = -1; double bd = P->match_radius * P->match_radius;
+      for (int j = 0; j < op->np; ++j) {
+        double d[3] = {op->local[j][0] - pr->local[i][0], op->local[j][1] - pr->local[i][1],
+                       op->local[j][2] - pr->local[i][2]};
+        double s = dot3(d, d);
+        if (s <= bd) { bd = s; best = j; }
+      }
+      if (best >= 0) memcpy(pr->lam[i], op->lam[best], sizeof(double) * 3);
+    }
+  }
+}
+
+/* Relative velocity of B with respect to A at the point, along dir. */
+static double rel_vel(const or_body* A, const or_body* B, const double* rA, const double* rB, const double* d) {
+  double wa[3], wb[3];
+  cross3(A->w, rA, wa); cross3(B->w, rB, wb);
+  double v[3] = {B->v[0] + wb[0] - A->v[0] - wa[0], B->v[1] + wb[1] - A->v[1] - wa[1],
+                 B->v[2] + wb[2] - A->v[2] - wa[2]};
+  return dot3(v, d);
+}
+
+/* Reading of the impulse application: the full 12-DOF impulse acts on both the
+   linear and the angular velocity of A (-) and B (+). */
+static void apply_impulse(or_body* A, or_body* B, const double* rA, const double* rB, const double* Pv) {
+  double t[3], u[3];
+  axpy3(-A->invm, Pv, A->v);
+  cross3(rA, Pv, t); matvec3(A->Iw, t, u); axpy3(-1.0, u, A->w);
+  axpy3(B->invm, Pv, B->v);
+  cross3(rB, Pv, t); matvec3(B->Iw, t, u); axpy3(1.0, u, B->w);
+}
+
+static void apply_warm_start(or_episode* E) {
+  for (int c = 0; c < E->np; ++c) {
+    or_pair* pr = &E->pairs[c];
+    or_body *A = body_ref(E, pr->a), *B = body_ref(E, pr->b);
+    for (int i = 0; i < pr->np; ++i) {
+      double Pv[3] = {0, 0, 0};
+      axpy3(pr->lam[i][0], pr->n, Pv); axpy3(pr->lam[i][1], pr->t1, Pv); axpy3(pr->lam[i][2], pr->t2, Pv);
+      apply_impulse(A, B, pr->rA[i], pr->rB[i], Pv);
+    }
+  }
+}
+
+/* One Gauss-Seidel sweep: Eq. lambda_n (restitution factor applied every
+   iteration, as in the listing; bias added for speculative points) and
+   Eq. coulomb_pgs (box clip with the just-updated normal impulse). */
+static void pgs_sweep(or_episode* E, double e) {
+  for (int c = 0; c < E->np; ++c) {
+    or_pair* pr = &E->pairs[c];
+    or_body *A = body_ref(E, pr->a), *B = body_ref(E, pr->b);
+    const double* dirs[3] = {pr->n, pr->t1, pr->t2};
+    for (int i = 0; i < pr->np; ++i) {
+      for (int r = 0; r < 3; ++r) {
+        double vrel = rel_vel(A, B, pr->rA[i], pr->rB[i], dirs[r]);
+        double old = pr->lam[i][r], nw;
+        if (r == 0) {
+          nw = fmax(0.0, old - (1.0 + e) * (vrel + pr->bias[i]) / pr->k[i][0]);
+        } else {
+          double lim = pr->mu * pr->lam[i][0];
+          nw = clampd(old - vrel / pr->k[i][r], -lim, lim);
+        }
+        pr->lam[i][r] = nw;
+        double Pv[3] = {(nw - old) * dirs[r][0], (nw - old) * dirs[r][1], (nw - old) * dirs[r][2]};
+        apply_impulse(A, B, pr->rA[i], pr->rB[i], Pv);
+      }
+    }
+  }
+}
+
+/* Reading of the PGS residual (m/s): max over rows of k |P(lambda - (v+b)/k) - lambda|
+   with P the row's projection (normal: [0, inf); tangents: [-mu ln, mu ln]),
+   evaluated at the current state without updating it. */
+static double pgs_residual(or_episode* E) {
+  double r = 0;
+  for (int c = 0; c < E->np; ++c) {
+    or_pair* pr = &E->pairs[c];
+    or_body *A = body_ref(E, pr->a), *B = body_ref(E, pr->b);
+    const double* dirs[3] = {pr->n, pr->t1, pr->t2};
+    for (int i = 0; i < pr->np; ++i)
+      for (int k = 0; k < 3; ++k) {
+        double vrel = rel_vel(A, B, pr->rA[i], pr->rB[i], dirs[k]);
+        double l = pr->lam[i][k], proj;
+        if (k == 0) proj = fmax(0.0, l - (vrel + pr->bias[i]) / pr->k[i][0]);
+        else {
+          double lim = pr->mu * pr->lam[i][0];
+          proj = clampd(l - vrel / pr->k[i][k], -lim, lim);
+        }
+        double rr = pr->k[i][k] * fabs(proj - l);
+        if (!(rr <= r)) r = rr;   /* propagates NaN */
+      }
+  }
+  return r;
+}
+
+static void solve(or_episode* E, const or_params* P) {
+  int sweeps = 0;
+  double res = 0;
+  if (E->np > 0) {
+    if (P->residual_tol > 0) {
+      for (;;) {
+        pgs_sweep(E, P->restitution);
+        ++sweeps;
+        if (sweeps >= P->pgs_min_iters) {
+          res = pgs_residual(E);
+          if (res <= P->residual_tol) break;
+          if (!(res == res)) break;
+        }
+        if (sweeps >= P->pgs_iter_cap) { E->status |= OR_STATUS_NOT_CONVERGED; break; }
+      }
+    } else {
+      for (int s = 0; s < P->pgs_iters; ++s) pgs_sweep(E, P->restitution);
+      sweeps = P->pgs_iters;
+      res = pgs_residual(E);
+    }
+  }
+  E->last_sweeps = sweeps;
+  E->last_res = res;
+  if (res > E->max_res) E->max_res = res;
+  E->total_sweeps += sweeps;
+  E->solves += 1;
+}
+
+/* Sec. 4.2 position update and Eq. quat_int with world-frame omega
+   (reading: q_dot = 1/2 [0, w] (x) q), renormalised. */
+static void integrate(or_episode* E, double h) {
+  for (int i = 0; i < E->nb; ++i) {
+    or_body* B = &E->b[i];
+    if (!B->active || B->is_static) continue;
+    axpy3(h, B->v, B->x);
+    double w0 = 0, w1 = B->w[0], w2 = B->w[1], w3 = B->w[2];
+    double q0 = B->q[0], q1 = B->q[1], q2 = B->q[2], q3 = B->q[3];
+    /* Hamilton product [0, w] (x) q */
+    double d0 = w0 * q0 - w1 * q1 - w2 * q2 - w3 * q3;
+    double d1 = w0 * q1 + w1 * q0 + w2 * q3 - w3 * q2;
+    double d2 = w0 * q2 - w1 * q3 + w2 * q0 + w3 * q1;
+    double d3 = w0 * q3 + w1 * q2 - w2 * q1 + w3 * q0;
+    double nq[4] = {q0 + 0.5 * h * d0, q1 + 0.5 * h * d1, q2 + 0.5 * h * d2, q3 + 0.5 * h * d3};
+    double l = sqrt(nq[0] * nq[0] + nq[1] * nq[1] + nq[2] * nq[2] + nq[3] * nq[3]);
+    for (int k = 0; k < 4; ++k) B->q[k] = nq[k] / l;
+  }
+}
+
+/* Eq. baumgarte, reading: dx_A = -beta max(0, depth - slop) m_A^-1/(m_A^-1 + m_B^-1) n,
+   dx_B = +(same with m_B^-1); depth = the pair's deepest point of this substep's
+   narrowphase; Jacobi-accumulated over pairs, then applied; translation only. */
+static void baumgarte(or_episode* E, const or_params* P) {
+  int nb = E->nb;
+  double (*dx)[3] = (double(*)[3])calloc(nb > 0 ? nb : 1, sizeof(double) * 3);
+  for (int c = 0; c < E->np; ++c) {
+    or_pair* pr = &E->pairs[c];
+    or_body *A = body_ref(E, pr->a), *B = body_ref(E, pr->b);
+    double pen = pr->depth_max - P->slop;
+    double wsum = A->invm + B->invm;
+    if (pen <= 0 || wsum <= 0) continue;
+    double s = P->beta * pen / wsum;
+    if (pr->a >= 0) axpy3(-s * A->invm, pr->n, dx[pr->a]);
+    axpy3(s * B->invm, pr->n, dx[pr->b]);
+  }
+  for (int i = 0; i < nb; ++i)
+    if (E->b[i].active && !E->b[i].is_static) axpy3(1.0, dx[i], E->b[i].x);
+  free(dx);
+}
+
+static void save_cache(or_episode* E) {
+  if (E->capprev < E->np) {
+    E->capprev = E->np;
+    E->prev = (or_pair*)realloc(E->prev, sizeof(or_pair) * (E->capprev > 0 ? E->capprev : 1));
+  }
+  if (E->np) memcpy(E->prev, E->pairs, sizeof(or_pair) * E->np);
+  E->nprev = E->np;
+}
+
+/* One substep of length h: forces, detection, setup, warm start, PGS,
+   integration, position correction. */
+static void substep(or_episode* E, const or_params* P, double h) {
+  for (int i = 0; i < E->nb; ++i) {
+    or_body* B = &E->b[i];
+    if (!B->active || B->is_static) continue;
+    /* Sec. 4.2: v += h (g + F/m); reading: no gyroscopic term in the integrator */
+    for (int k = 0; k < 3; ++k) B->v[k] += h * (P->gravity[k] + (B->f_steps > 0 ? B->f[k] * B->invm : 0.0));
+  }
+  for (int i = 0; i < E->nb; ++i) update_frame(&E->b[i]);
+  detect(E, P);
+  setup(E, h);
+  warm_start_match(E, P);
+  apply_warm_start(E);
+  solve(E, P);
+  integrate(E, h);
+  baumgarte(E, P);
+  save_cache(E);
+}
+
+/* Sec. 8.3: E_k = sum 1/2 m |v|^2 + 1/2 w . I_world w. */
+static double kinetic(const or_body* B) {
+  double I[3], wl[3];
+  or_body_inertia(B->mass, B->half, I);
+  double R[3][3];
+  rotmat(B->q, R);
+  for (int k = 0; k < 3; ++k) wl[k] = R[0][k] * B->w[0] + R[1][k] * B->w[1] + R[2][k] * B->w[2];
+  return 0.5 * B->mass * dot3(B->v, B->v) + 0.5 * (I[0] * wl[0] * wl[0] + I[1] * wl[1] * wl[1] + I[2] * wl[2] * wl[2]);
+}
+
+/* Eq. collapse terms over active dynamic blocks, excluding `skip`.
+   Reading: dx = |x - x0|; theta = angle between the current and initial
+   thickness axes; fallen = dx > fall_frac * block length. */
+static void collapse_terms(or_episode* E, int skip, double* ek, double* dxr, double* th, int* nfallen, double ff) {
+  *ek = 0; *dxr = 0; *th = 0; *nfallen = 0;
+  for (int i = 0; i < E->nb; ++i) {
+    or_body* B = &E->b[i];
+    if (!B->active || B->is_static || i == skip) continue;
+    *ek += kinetic(B);
+    double d[3] = {B->x[0] - B->x0[0], B->x[1] - B->x0[1], B->x[2] - B->x0[2]};
+    double r = norm3(d) / (2 * B->half[0]);
+    if (r > *dxr) *dxr = r;
+    if (r > ff) (*nfallen)++;
+    double R[3][3]; rotmat(B->q, R);
+    double z[3]; col3(R, 2, z);
+    double c = clampd(dot3(z, B->z0), -1.0, 1.0);
+    double a = acos(c);
+    if (a > *th) *th = a;
+  }
+}
+
+static int count_dynamic(const or_episode* E) {
+  int n = 0;
+  for (int i = 0; i < E->nb; ++i) n += E->b[i].active && !E->b[i].is_static;
+  return n;
+}
+
+static int state_finite(const or_episode* E) {
+  for (int i = 0; i < E->nb; ++i) {
+    const or_body* B = &E->b[i];
+    for (int k = 0; k < 3; ++k)
+      if (!isfinite(B->x[k]) || !isfinite(B->v[k]) || !isfinite(B->w[k])) return 0;
+  }
+  return 1;
+}
+
+static void start_move(or_episode* E, const or_params* P) {
+  int m = E->mi;
+  int blk = E->mv_block[m];
+  or_body* B = &E->b[blk];
+  double R[3][3]; rotmat(B->q, R);
+  /* push axis: block Y = long axis (body x), block X = width axis (body y) */
+  double dir[3]; col3(R, E->mv_axis[m] == 1 ? 0 : 1, dir);
+  double g = norm3(P->gravity);
+  /* Sec. 5: threshold force F = k mu_s m g, scaled by the schedule's factor */
+  double F = E->mv_sign[m] * E->mv_factor[m] * E->mv_k[m] * B->mu * B->mass * g;
+  for (int k = 0; k < 3; ++k) B->f[k] = F * dir[k];
+  B->f_steps = E->mv_push[m];
+  E->pb = blk;
+  E->phase = OR_PH_PUSH;
+  E->remaining = E->mv_push[m];
+}
+
+static void end_push(or_episode* E) {
+  if (E->pb >= 0) {
+    or_body* B = &E->b[E->pb];
+    B->f[0] = B->f[1] = B->f[2] = 0; B->f_steps = 0;
+  }
+}
+
+/* One step (n_sub substeps) plus the episode schedule. */
+static void episode_step(or_episode* E, const or_params* P) {
+  E->body_steps += count_dynamic(E);
+  double h = P->dt / P->n_sub;
+  for (int s = 0; s < P->n_sub; ++s) substep(E, P, h);
+  for (int i = 0; i < E->nb; ++i)
+    if (E->b[i].f_steps > 0) E->b[i].f_steps--;
+  E->steps++;
+  if (!state_finite(E)) { E->status |= OR_STATUS_NONFINITE; E->phase = E->phase == OR_PH_FREE ? OR_PH_FREE : OR_PH_DONE; return; }
+  if (E->phase == OR_PH_FREE || E->phase == OR_PH_DONE) return;
+  double ek, dxr, th; int nf;
+  int skip = E->phase == OR_PH_PUSH ? E->pb : -1;
+  collapse_terms(E, skip, &ek, &dxr, &th, &nf, P->fall_frac);
+  int coll = dxr > P->fall_frac && ek > P->collapse_ek && th > P->collapse_theta_deg * OR_PI / 180.0;
+  if ((E->phase == OR_PH_PUSH || E->phase == OR_PH_SETTLE) && coll) {
+    E->collapsed = 1;
+    if (E->phase == OR_PH_PUSH) end_push(E);
+    E->pb = -1;
+    E->phase = OR_PH_REST;
+    E->rest_left = P->rest_steps;
+    return;
+  }
+  if (E->phase == OR_PH_PUSH) {
+    if (--E->remaining <= 0) {
+      end_push(E);
+      if (E->mv_remove[E->mi]) { E->b[E->pb].active = 0; }
+      E->pb = -1;
+      E->phase = OR_PH_SETTLE;
+      E->remaining = E->mv_settle[E->mi];
+      if (E->remaining <= 0) goto next_move;
+    }
+    return;
+  }
+  if (E->phase == OR_PH_SETTLE) {
+    if (--E->remaining <= 0) goto next_move;
+    return;
+  }
+  if (E->phase == OR_PH_REST) {
+    double eka, d1, d2; int n1;
+    collapse_terms(E, -1, &eka, &d1, &d2, &n1, P->fall_frac);
+    E->rest_left--;
+    if (eka < P->rest_ek) { E->resting = 1; E->phase = OR_PH_DONE; }
+    else if (E->rest_left <= 0) E->phase = OR_PH_DONE;
+    return;
+  }
+  return;
+next_move:
+  E->mi++;
+  if (E->mi < E->n_moves) start_move(E, P);
+  else E->phase = OR_PH_DONE;
+}
+
+/* ------------------------------------------------------------- public API -- */
+or_world* or_create(int n_episodes, const int* body_off, const double* half, const double* mass,
+                    const double* mu, const double* x, const double* q, const double* v,
+                    const double* w, const double* ground_mu, const or_params* p) {
+  or_world* W = (or_world*)calloc(1, sizeof(or_world));
+  W->E = n_episodes;
+  W->B = body_off[n_episodes];
+  W->P = *p;
+  W->body_off = (int*)malloc(sizeof(int) * (n_episodes + 1));
+  memcpy(W->body_off, body_off, sizeof(int) * (n_episodes + 1));
+  W->ep = (or_episode*)calloc(n_episodes > 0 ? n_episodes : 1, sizeof(or_episode));
+  int NB = W->B;
+  for (int e = 0; e < n_episodes; ++e) {
+    or_episode* E = &W->ep[e];
+    E->nb = body_off[e + 1] - body_off[e];
+    E->b = (or_body*)calloc(E->nb > 0 ? E->nb : 1, sizeof(or_body));
+    E->ground_mu = ground_mu[e];
+    E->ground.q[0] = 1;
+    update_frame(&E->ground);
+    E->phase = OR_PH_FREE;
+    E->pb = -1;
+    for (int i = 0; i < E->nb; ++i) {
+      int g = body_off[e] + i;
+      or_body* B = &E->b[i];
+      for (int k = 0; k < 3; ++k) {
+        B->x[k] = x[k * NB + g]; B->half[k] = half[k * NB + g];
+        B->v[k] = v ? v[k * NB + g] : 0; B->w[k] = w ? w[k * NB + g] : 0;
+      }
+      double ql = 0;
+      for (int k = 0; k < 4; ++k) { B->q[k] = q[k * NB + g]; ql += B->q[k] * B->q[k]; }
+      ql = sqrt(ql);
+      for (int k = 0; k < 4; ++k) B->q[k] /= ql;
+      B->mass = mass[g];
+      B->mu = mu[g];
+      B->active = 1;
+      B->is_static = !(mass[g] > 0);
+      if (!B->is_static) {
+        double I[3]; or_body_inertia(B->mass, B->half, I);
+        B->invm = 1.0 / B->mass;
+        for (int k = 0; k < 3; ++k) B->invI[k] = 1.0 / I[k];
+      } else {
+        B->v[0] = B->v[1] = B->v[2] = B->w[0] = B->w[1] = B->w[2] = 0;
+      }
+      update_frame(B);
+      memcpy(B->x0, B->x, sizeof B->x0);
+      col3(B->R, 2, B->z0);
+    }
+  }
+  return W;
+}
+
+void or_destroy(or_world* W) {
+  if (!W) return;
+  for (int e = 0; e < W->E; ++e) { free(W->ep[e].b); free(W->ep[e].pairs); free(W->ep[e].prev); }
+  free(W->ep); free(W->body_off);
+  free(W->m_block); free(W->m_axis); free(W->m_remove); free(W->m_push); free(W->m_settle);
+  free(W->m_sign); free(W->m_factor); free(W->m_k);
+  free(W);
+}
+
+int or_set_protocol(or_world* W, const int* off, const int* block, const int* axis, const double* sign,
+                    const double* factor, const double* k, const int* remove, const int* push_steps,
+                    const int* settle_steps) {
+  int M = off[W->E];
+  size_t n = (size_t)(M > 0 ? M : 1);
+#define DUP(dst, src, T) do { dst = (T*)malloc(sizeof(T) * n); if (M) memcpy(dst, src, sizeof(T) * M); } while (0)
+  DUP(W->m_block, block, int); DUP(W->m_axis, axis, int); DUP(W->m_remove, remove, int);
+  DUP(W->m_push, push_steps, int); DUP(W->m_settle, settle_steps, int);
+  DUP(W->m_sign, sign, double); DUP(W->m_factor, factor, double); DUP(W->m_k, k, double);
+#undef DUP
+  for (int e = 0; e < W->E; ++e) {
+    or_episode* E = &W->ep[e];
+    int o = off[e];
+    E->n_moves = off[e + 1] - o;
+    for (int m = 0; m < E->n_moves; ++m)
+      if (block[o + m] < 0 || block[o + m] >= E->nb) return -1;
+    E->mv_block = W->m_block + o; E->mv_axis = W->m_axis + o; E->mv_remove = W->m_remove + o;
+    E->mv_push = W->m_push + o; E->mv_settle = W->m_settle + o;
+    E->mv_sign = W->m_sign + o; E->mv_factor = W->m_factor + o; E->mv_k = W->m_k + o;
+    E->mi = 0;
+    if (E->n_moves > 0) start_move(E, &W->P);
+    else E->phase = OR_PH_DONE;
+  }
+  return 0;
+}
+
+int or_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+int or_run_protocol(or_world* W, int max_steps, int n_threads) {
+  int maxs = 0;
+#ifdef _OPENMP
+  if (n_threads <= 0) n_threads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads) reduction(max : maxs)
+#endif
+  for (int e = 0; e < W->E; ++e) {
+    or_episode* E = &W->ep[e];
+    int s = 0;
+    while (s < max_steps && E->phase != OR_PH_DONE && E->phase != OR_PH_FREE) { episode_step(E, &W->P); ++s; }
+    if (s > maxs) maxs = s;
+  }
+  (void)n_threads;
+  return maxs;
+}
+
+void or_step(or_world* W, int n_steps, int n_threads) {
+#ifdef _OPENMP
+  if (n_threads <= 0) n_threads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads)
+#endif
+  for (int e = 0; e < W->E; ++e)
+    for (int s = 0; s < n_steps; ++s) episode_step(&W->ep[e], &W->P);
+  (void)n_threads;
+}
+
+int or_apply_push(or_world* W, int e, int blk, int axis, double force, int n_steps) {
+  if (e < 0 || e >= W->E || blk < 0 || blk >= W->ep[e].nb) return -1;
+  or_body* B = &W->ep[e].b[blk];
+  double R[3][3]; rotmat(B->q, R);
+  double dir[3]; col3(R, axis == 1 ? 0 : 1, dir);
+  for (int k = 0; k < 3; ++k) B->f[k] = force * dir[k];
+  B->f_steps = n_steps;
+  return 0;
+}
+
+int or_remove_block(or_world* W, int e, int blk) {
+  if (e < 0 || e >= W->E || blk < 0 || blk >= W->ep[e].nb) return -1;
+  W->ep[e].b[blk].active = 0;
+  return 0;
+}
+
+int or_active(const or_world* W, int g) {
+  for (int e = 0; e < W->E; ++e)
+    if (g < W->body_off[e + 1]) return W->ep[e].b[g - W->body_off[e]].active;
+  return 0;
+}
+
+void or_get_state(const or_world* W, double* x, double* q, double* v, double* w) {
+  int NB = W->B;
+  for (int e = 0; e < W->E; ++e)
+    for (int i = 0; i < W->ep[e].nb; ++i) {
+      int g = W->body_off[e] + i;
+      const or_body* B = &W->ep[e].b[i];
+      for (int k = 0; k < 3; ++k) {
+        if (x) x[k * NB + g] = B->x[k];
+        if (v) v[k * NB + g] = B->v[k];
+        if (w) w[k * NB + g] = B->w[k];
+      }
+      if (q) for (int k = 0; k < 4; ++k) q[k * NB + g] = B->q[k];
+    }
+}
+
+void or_set_state(or_world* W, const double* x, const double* q, const double* v, const double* w) {
+  int NB = W->B;
+  for (int e = 0; e < W->E; ++e)
+    for (int i = 0; i < W->ep[e].nb; ++i) {
+      int g = W->body_off[e] + i;
+      or_body* B = &W->ep[e].b[i];
+      for (int k = 0; k < 3; ++k) {
+        if (x) B->x[k] = x[k * NB + g];
+        if (v && !B->is_static) B->v[k] = v[k * NB + g];
+        if (w && !B->is_static) B->w[k] = w[k * NB + g];
+      }
+      if (q) {
+        double l = 0;
+        for (int k = 0; k < 4; ++k) { B->q[k] = q[k * NB + g]; l += B->q[k] * B->q[k]; }
+        l = sqrt(l);
+        for (int k = 0; k < 4; ++k) B->q[k] /= l;
+      }
+      update_frame(B);
+    }
+}
+
+void or_clear_cache(or_world* W) {
+  for (int e = 0; e < W->E; ++e) W->ep[e].nprev = 0;
+}
+
+static void write_crec(const or_pair* pr, double* o) {
+  memset(o, 0, sizeof(double) * OR_CREC);
+  o[0] = pr->a; o[1] = pr->b; o[2] = pr->axis; o[3] = pr->ref_face; o[4] = pr->inc_face; o[5] = pr->np;
+  for (int k = 0; k < 3; ++k) { o[6 + k] = pr->n[k]; o[9 + k] = pr->t1[k]; }
+  o[12] = pr->delta; o[13] = pr->mu; o[14] = pr->depth_max;
+  for (int i = 0; i < pr->np; ++i) {
+    double* r = o + 15 + 10 * i;
+    for (int k = 0; k < 3; ++k) { r[k] = pr->p[i][k]; r[4 + k] = pr->lam[i][k]; r[7 + k] = pr->local[i][k]; }
+    r[3] = pr->depth[i];
+  }
+}
+
+int or_get_contacts(const or_world* W, int e, double* out, int cap) {
+  if (e < 0 || e >= W->E) return -1;
+  const or_episode* E = &W->ep[e];
+  /* the cache holds the last substep's pairs with their final impulses */
+  for (int c = 0; c < E->nprev && c < cap; ++c) write_crec(&E->prev[c], out + (size_t)c * OR_CREC);
+  return E->nprev;
+}
+
+/* Eq. stability: support polygon = convex hull (Andrew's monotone chain) of
+   the xy corners of ground-touching blocks; d = min signed distance from the
+   COM to the hull edges, positive inside.  Reading for degenerate hulls
+   (fewer than 3 vertices): minus the distance to the segment or point. */
+static int cmp_xy(const void* a, const void* b) {
+  const double *p = (const double*)a, *q = (const double*)b;
+  if (p[0] != q[0]) return p[0] < q[0] ? -1 : 1;
+  if (p[1] != q[1]) return p[1] < q[1] ? -1 : 1;
+  return 0;
+}
+static double cross2(const double* o, const double* a, const double* b) {
+  return (a[0] - o[0]) * (b[1] - o[1]) - (a[1] - o[1]) * (b[0] - o[0]);
+}
+double or_support_margin(int n, const double* xy, const double* com) {
+  if (n <= 0) return -INFINITY;
+  double* P = (double*)malloc(sizeof(double) * 2 * n);
+  memcpy(P, xy, sizeof(double) * 2 * n);
+  qsort(P, n, sizeof(double) * 2, cmp_xy);
+  double* H = (double*)malloc(sizeof(double) * 2 * (2 * n + 1));
+  int k = 0;
+  for (int i = 0; i < n; ++i) {
+    while (k >= 2 && cross2(H + 2 * (k - 2), H + 2 * (k - 1), P + 2 * i) <= 0) --k;
+    H[2 * k] = P[2 * i]; H[2 * k + 1] = P[2 * i + 1]; ++k;
+  }
+  for (int i = n - 2, t = k + 1; i >= 0; --i) {
+    while (k >= t && cross2(H + 2 * (k - 2), H + 2 * (k - 1), P + 2 * i) <= 0) --k;
+    H[2 * k] = P[2 * i]; H[2 * k + 1] = P[2 * i + 1]; ++k;
+  }
+  int m = k > 1 ? k - 1 : k;   /* hull vertices, counter-clockwise */
+  double d;
+  if (m >= 3) {
+    d = INFINITY;
+    for (int i = 0; i < m; ++i) {
+      const double *a = H + 2 * i, *b = H + 2 * ((i + 1) % m);
+      double ex = b[0] - a[0], ey = b[1] - a[1];
+      double s = (ex * (com[1] - a[1]) - ey * (com[0] - a[0])) / sqrt(ex * ex + ey * ey);
+      if (s < d) d = s;
+    }
+  } else if (m == 2) {
+    const double *a = H, *b = H + 2;
+    double ex = b[0] - a[0], ey = b[1] - a[1];
+    double l2 = ex * ex + ey * ey;
+    double t = l2 > 0 ? clampd(((com[0] - a[0]) * ex + (com[1] - a[1]) * ey) / l2, 0, 1) : 0;
+    double dx = com[0] - (a[0] + t * ex), dy = com[1] - (a[1] + t * ey);
+    d = -sqrt(dx * dx + dy * dy);
+  } else {
+    double dx = com[0] - H[0], dy = com[1] - H[1];
+    d = -sqrt(dx * dx + dy * dy);
+  }
+  free(P); free(H);
+  return d;
+}
+
+double or_com_imbalance(const or_world* W, int e) {
+  const or_episode* E = &W->ep[e];
+  const double eps = W->P.aabb_eps;
+  double com[2] = {0, 0}, mt = 0;
+  double* xy = (double*)malloc(sizeof(double) * 16 * (E->nb > 0 ? E->nb : 1));
+  int n = 0;
+  for (int i = 0; i < E->nb; ++i) {
+    const or_body* B = &E->b[i];
+    if (!B->active || B->is_static) continue;
+    com[0] += B->mass * B->x[0]; com[1] += B->mass * B->x[1]; mt += B->mass;
+    double R[3][3]; rotmat(B->q, R);
+    double ez = fabs(R[2][0]) * B->half[0] + fabs(R[2][1]) * B->half[1] + fabs(R[2][2]) * B->half[2];
+    if (B->x[2] - ez > eps) continue;
+    for (int c = 0; c < 8; ++c) {
+      double s0 = (c & 1) ? 1 : -1, s1 = (c & 2) ? 1 : -1, s2 = (c & 4) ? 1 : -1;
+      for (int k = 0; k < 2; ++k)
+        xy[2 * n + k] = B->x[k] + s0 * B->half[0] * R[k][0] + s1 * B->half[1] * R[k][1] + s2 * B->half[2] * R[k][2];
+      ++n;
+    }
+  }
+  double r;
+  if (mt <= 0 || n == 0) r = 0;
+  else {
+    com[0] /= mt; com[1] /= mt;
+    r = -or_support_margin(n, xy, com);
+  }
+  free(xy);
+  return r;
+}
+
+void or_get_stats(or_world* W, double* out) {
+  for (int e = 0; e < W->E; ++e) {
+    or_episode* E = &W->ep[e];
+    double* o = out + (size_t)e * OR_NSTAT;
+    double ek, dxr, th; int nf;
+    collapse_terms(E, -1, &ek, &dxr, &th, &nf, W->P.fall_frac);
+    int npts = 0;
+    for (int c = 0; c < E->nprev; ++c) npts += E->prev[c].np;
+    o[OR_ST_STATUS] = E->status; o[OR_ST_COLLAPSED] = E->collapsed;
+    o[OR_ST_RESTING] = E->resting || ek < W->P.rest_ek; o[OR_ST_NFALLEN] = nf;
+    o[OR_ST_COM_IMB] = or_com_imbalance(W, e); o[OR_ST_EK] = ek;
+    o[OR_ST_LAST_RES] = E->last_res; o[OR_ST_LAST_SWEEPS] = E->last_sweeps;
+    o[OR_ST_TOTAL_SWEEPS] = (double)E->total_sweeps; o[OR_ST_SOLVES] = (double)E->solves;
+    o[OR_ST_STEPS] = (double)E->steps; o[OR_ST_BODY_STEPS] = E->body_steps;
+    o[OR_ST_PHASE] = E->phase; o[OR_ST_MOVES_DONE] = E->mi; o[OR_ST_NPAIRS] = E->nprev;
+    o[OR_ST_NPOINTS] = npts; o[OR_ST_MAX_RES] = E->max_res;
+  }
+}
+
+/* ------------------------------------------------------- stage entry points */
+static void mkbox(const double* x, const double* q, const double* h, box_t* b) {
+  double qq[4], l = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  for (int k = 0; k < 4; ++k) qq[k] = q[k] / l;
+  memcpy(b->x, x, sizeof b->x); memcpy(b->h, h, sizeof b->h);
+  rotmat(qq, b->R);
+}
+
+int or_sat(const double* xA, const double* qA, const double* hA, const double* xB, const double* qB,
+           const double* hB, double margin, double* delta15, int* valid15, int* axis, double* n, double* dmin) {
+  box_t A, B; mkbox(xA, qA, hA, &A); mkbox(xB, qB, hB, &B);
+  double U[15][3];
+  sat15(&A, &B, delta15, valid15, U);
+  int ax = sat_select(delta15, valid15, dmin);
+  double d[3] = {B.x[0] - A.x[0], B.x[1] - A.x[1], B.x[2] - A.x[2]};
+  double s = dot3(U[ax], d) < 0 ? -1 : 1;
+  for (int k = 0; k < 3; ++k) n[k] = s * U[ax][k];
+  *axis = ax;
+  return *dmin > -margin;
+}
+
+int or_pair_manifold(const double* xA, const double* qA, const double* hA, const double* xB, const double* qB,
+                     const double* hB, double margin, double* out) {
+  box_t A, B; mkbox(xA, qA, hA, &A); mkbox(xB, qB, hB, &B);
+  or_pair pr; memset(&pr, 0, sizeof pr);
+  int ok = box_pair(&A, &B, margin, &pr, NULL);
+  pr.a = 0; pr.b = 1;
+  if (ok) tangent_basis(pr.n, pr.t1, pr.t2);
+  write_crec(&pr, out);
+  return ok ? pr.np : 0;
+}
+
+int or_ground_manifold(const double* x, const double* q, const double* h, double margin, double* out) {
+  box_t B; mkbox(x, q, h, &B);
+  or_pair pr; memset(&pr, 0, sizeof pr);
+  int ok = ground_pair(&B, margin, &pr);
+  pr.a = -1; pr.b = 0;
+  if (ok) tangent_basis(pr.n, pr.t1, pr.t2);
+  write_crec(&pr, out);
+  return ok ? pr.np : 0;
+}

@@ -1,0 +1,443 @@
+"""Pins of the FP64 oracle against closed forms, brute force and the paper's
+printed numbers (CPU only).  Each pin is chosen so that a plausible mistake in
+the oracle (a dropped term, a flipped sign, a transposed operand, a wrong
+product order) fails at least one of them."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+G = 9.81
+H = 1.0 / 240.0
+HALF = (0.0375, 0.0125, 0.0075)          # 0.075 x 0.025 x 0.015 m block
+
+
+def qaxis(axis, ang):
+    axis = np.asarray(axis, float) / np.linalg.norm(axis)
+    return np.r_[math.cos(ang / 2), math.sin(ang / 2) * axis]
+
+
+def qmul(a, b):
+    w1, x1, y1, z1 = a
+    w2, x2, y2, z2 = b
+    return np.array([w1 * w2 - x1 * x2 - y1 * y2 - z1 * z2, w1 * x2 + x1 * w2 + y1 * z2 - z1 * y2,
+                     w1 * y2 - x1 * z2 + y1 * w2 + z1 * x2, w1 * z2 + x1 * y2 - y1 * x2 + z1 * w2])
+
+
+def rodrigues(axis, ang):
+    k = np.asarray(axis, float) / np.linalg.norm(axis)
+    K = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
+    return np.eye(3) + math.sin(ang) * K + (1 - math.cos(ang)) * K @ K
+
+
+def one_box_world(x, q=(1, 0, 0, 0), v=(0, 0, 0), w=(0, 0, 0), mass=0.015, half=HALF, mu=0.4, **prm):
+    sc = synth.custom_scene([dict(half=half, x=x, q=q, v=v, w=w, mass=mass, mu=mu)], ground_mu=mu)
+    # keep the oracle in FP64 for closed forms: overwrite the float32 scene arrays
+    sc.half = np.array(half, float).reshape(3, 1); sc.x = np.array(x, float).reshape(3, 1)
+    sc.q = np.array(q, float).reshape(4, 1); sc.v = np.array(v, float).reshape(3, 1)
+    sc.w = np.array(w, float).reshape(3, 1); sc.mass = np.array([mass], float)
+    sc.mu = np.array([mu], float); sc.ground_mu = np.array([mu], float)
+    return oracle.World(sc, synth.params(**prm))
+
+
+# ------------------------------------------------------------- Sec. 4 closed forms
+def test_free_fall_discrete_closed_form():
+    W = one_box_world((0.1, -0.2, 2.0), v=(0.3, 0.0, 0.0))
+    n = 37
+    W.step(n)
+    x, _, v, _ = W.state()
+    # semi-implicit Euler: v_n = v0 - g n h, z_n = z0 - g h^2 n (n + 1) / 2
+    assert abs(v[2, 0] - (-G * n * H)) < 1e-12
+    assert abs(x[2, 0] - (2.0 - G * H * H * n * (n + 1) / 2)) < 1e-12
+    assert abs(x[0, 0] - (0.1 + 0.3 * n * H)) < 1e-12
+
+
+def test_rotation_matrix_textbook():
+    th = 0.7
+    R = oracle.rotmat(qaxis((0, 0, 1), th))
+    assert np.allclose(R, [[math.cos(th), -math.sin(th), 0], [math.sin(th), math.cos(th), 0], [0, 0, 1]], atol=1e-15)
+    rng = np.random.default_rng(1)
+    for _ in range(50):
+        q = rng.normal(size=4); q /= np.linalg.norm(q)
+        R = oracle.rotmat(q)
+        assert np.allclose(R @ R.T, np.eye(3), atol=1e-12)
+        assert abs(np.linalg.det(R) - 1) < 1e-12
+        ax = q[1:] / np.linalg.norm(q[1:])
+        assert np.allclose(R, rodrigues(ax, 2 * math.atan2(np.linalg.norm(q[1:]), q[0])), atol=1e-12)
+
+
+def test_quaternion_integration_world_frame_closed_form():
+    # constant world-frame omega, no contacts, no gravity: each step is the exact
+    # rotation by 2 atan(|w| h / 2) about the world axis (Eq. quat_int + renormalisation)
+    q0 = qmul(qaxis((1, 2, 3), 0.9), qaxis((0, 1, 0), 0.4))
+    wv = np.array([0.3, -1.1, 2.0])
+    W = one_box_world((0, 0, 5.0), q=q0, w=wv, gravity=(0.0, 0.0, 0.0))
+    n = 50
+    W.step(n)
+    _, q, _, w = W.state()
+    ang = 2 * n * math.atan(np.linalg.norm(wv) * H / 2)
+    R_expect = rodrigues(wv, ang) @ oracle.rotmat(q0)
+    assert np.allclose(oracle.rotmat(q[:, 0]), R_expect, atol=1e-12)
+    assert np.allclose(w[:, 0], wv, atol=1e-15)   # no gyroscopic term in the integrator
+
+
+def test_box_inertia_closed_form_and_numeric():
+    I = oracle.body_inertia(12.0, [0.5, 1.0, 1.5])          # 1 x 2 x 3 box
+    assert np.allclose(I, [13.0, 10.0, 5.0], rtol=0, atol=1e-12)
+    # midpoint-rule integral of a uniform box: I_xx = rho * int (y^2 + z^2) dV
+    hx, hy, hz = HALF
+    m = 0.015
+    n = 40
+    g = lambda h: (np.arange(n) + 0.5) / n * 2 * h - h
+    X, Y, Z = np.meshgrid(g(hx), g(hy), g(hz), indexing="ij")
+    dm = m / X.size
+    num = dm * np.array([(Y**2 + Z**2).sum(), (X**2 + Z**2).sum(), (X**2 + Y**2).sum()])
+    assert np.allclose(oracle.body_inertia(m, HALF), num, rtol=2e-3)
+
+
+# ----------------------------------------------------------------- Sec. 6.2 SAT
+def random_box(rng, aligned=False):
+    h = rng.uniform(0.005, 0.05, size=3)
+    if aligned:
+        q = [qaxis((0, 0, 1), 0.0), qaxis((0, 0, 1), math.pi / 2), qaxis((1, 0, 0), math.pi / 2)][rng.integers(3)]
+    else:
+        q = rng.normal(size=4); q /= np.linalg.norm(q)
+    return h, q
+
+
+def planes(x, q, h):
+    R = oracle.rotmat(q)
+    N, c = [], []
+    for i in range(3):
+        for s in (1, -1):
+            n = s * R[:, i]
+            N.append(n); c.append(n @ x + h[i])
+    return np.array(N), np.array(c)
+
+
+def boxes_intersect_bruteforce(xa, qa, ha, xb, qb, hb):
+    """Vertex enumeration over all C(12, 3) = 220 plane triples of the 12 face
+    planes: the intersection is non-empty iff some triple's point satisfies all 12."""
+    Na, ca = planes(xa, qa, ha)
+    Nb, cb = planes(xb, qb, hb)
+    N = np.vstack([Na, Nb]); c = np.r_[ca, cb]
+    idx = np.array([(i, j, k) for i in range(12) for j in range(i + 1, 12) for k in range(j + 1, 12)])
+    A = N[idx]
+    det = np.linalg.det(A)
+    ok = np.abs(det) > 1e-12
+    pts = np.linalg.solve(A[ok], c[idx[ok]][..., None])[..., 0]
+    feas = (pts @ N.T <= c + 1e-12).all(axis=1)
+    return bool(feas.any())
+
+
+def test_sat_matches_vertex_enumeration():
+    rng = np.random.default_rng(2024)
+    n_hit = n_miss = 0
+    for t in range(1500):
+        ha, qa = random_box(rng, aligned=t % 5 == 0)
+        hb, qb = random_box(rng, aligned=t % 5 == 0)
+        xa = np.zeros(3)
+        xb = rng.normal(size=3) * 0.04
+        r = oracle.sat(xa, qa, ha, xb, qb, hb, margin=0.0)
+        if abs(r["dmin"]) < 1e-9:
+            continue
+        truth = boxes_intersect_bruteforce(xa, qa, ha, xb, qb, hb)
+        assert (r["dmin"] > 0) == truth, (t, r["dmin"])
+        n_hit += truth; n_miss += not truth
+    assert n_hit > 200 and n_miss > 200
+
+
+def fib_sphere(n):
+    i = np.arange(n) + 0.5
+    phi = np.arccos(1 - 2 * i / n)
+    th = math.pi * (1 + 5 ** 0.5) * i
+    return np.stack([np.cos(th) * np.sin(phi), np.sin(th) * np.sin(phi), np.cos(phi)], 1)
+
+
+def overlap_dirs(U, xa, qa, ha, xb, qb, hb):
+    Ra, Rb = oracle.rotmat(qa), oracle.rotmat(qb)
+    d = xb - xa
+    return (np.abs(U @ Ra) @ ha + np.abs(U @ Rb) @ hb - np.abs(U @ d))
+
+
+def test_sat_depth_is_minimum_over_all_directions():
+    """For overlapping boxes the penetration depth min_u [r_A(u) + r_B(u) - |d.u|]
+    over the whole sphere is attained on one of the 15 SAT axes: sampled
+    directions never go below the SAT minimum and a local search reaches it."""
+    from scipy.optimize import minimize
+    rng = np.random.default_rng(7)
+    U = fib_sphere(40000)
+    checked = 0
+    for t in range(120):
+        ha, qa = random_box(rng)
+        hb, qb = random_box(rng)
+        xa = np.zeros(3)
+        xb = rng.normal(size=3) * 0.02
+        r = oracle.sat(xa, qa, ha, xb, qb, hb, margin=0.0)
+        if r["dmin"] <= 1e-4:
+            continue
+        f = overlap_dirs(U, xa, qa, ha, xb, qb, hb)
+        assert f.min() >= r["dmin"] - 1e-12
+        best = np.inf
+        for j in np.argsort(f)[:6]:
+            def fun(p):
+                u = np.array([math.sin(p[0]) * math.cos(p[1]), math.sin(p[0]) * math.sin(p[1]), math.cos(p[0])])
+                return overlap_dirs(u[None], xa, qa, ha, xb, qb, hb)[0]
+            u0 = U[j]
+            p0 = [math.acos(np.clip(u0[2], -1, 1)), math.atan2(u0[1], u0[0])]
+            res = minimize(fun, p0, method="Nelder-Mead", options=dict(xatol=1e-12, fatol=1e-14, maxiter=4000))
+            best = min(best, res.fun)
+        assert best >= r["dmin"] - 1e-12
+        assert best - r["dmin"] < 1e-6 * max(1.0, r["dmin"] * 100), (t, best, r["dmin"])
+        checked += 1
+    assert checked > 40
+
+
+def test_sat_all_15_axes_explicit():
+    rng = np.random.default_rng(3)
+    for _ in range(200):
+        ha, qa = random_box(rng); hb, qb = random_box(rng)
+        xa = rng.normal(size=3) * 0.01; xb = rng.normal(size=3) * 0.03
+        r = oracle.sat(xa, qa, ha, xb, qb, hb)
+        Ra, Rb = oracle.rotmat(qa), oracle.rotmat(qb)
+        axes = [Ra[:, i] for i in range(3)] + [Rb[:, i] for i in range(3)]
+        axes += [np.cross(Ra[:, i], Rb[:, j]) for i in range(3) for j in range(3)]
+        for k, u in enumerate(axes):
+            l = np.linalg.norm(u)
+            if l < 1e-6:
+                assert not r["valid"][k]
+                continue
+            u = u / l
+            dk = ha @ np.abs(Ra.T @ u) + hb @ np.abs(Rb.T @ u) - abs((xb - xa) @ u)
+            assert abs(r["delta"][k] - dk) < 1e-13
+        assert abs(r["dmin"] - r["delta"][r["valid"]].min()) < 1e-15
+        assert r["n"] @ (xb - xa) >= 0
+
+
+# ------------------------------------------------------------ Sec. 6.2.1 manifold
+def test_manifold_block_on_block_same_orientation():
+    pen = 2e-4
+    hx, hy, hz = HALF
+    m = oracle.pair_manifold(np.zeros(3), [1, 0, 0, 0], HALF, [0, 0, 2 * hz - pen], [1, 0, 0, 0], HALF)
+    assert m["np"] == 4 and m["axis"] == 2
+    assert np.allclose(m["n"], [0, 0, 1])
+    assert np.allclose(sorted(map(tuple, np.round(m["p"], 12))),
+                       sorted([(sx * hx, sy * hy, hz - pen / 2) for sx in (-1, 1) for sy in (-1, 1)]), atol=1e-12)
+    assert np.allclose(m["depth"], pen, atol=1e-13)
+
+
+def test_manifold_crossed_blocks_square():
+    pen = 1e-4
+    hx, hy, hz = HALF
+    qb = qaxis((0, 0, 1), math.pi / 2)
+    m = oracle.pair_manifold(np.zeros(3), [1, 0, 0, 0], HALF, [0.003, -0.002, 2 * hz - pen], qb, HALF)
+    assert m["np"] == 4 and m["axis"] == 2
+    exp = sorted([(0.003 + sx * hy, sy * hy, hz - pen / 2) for sx in (-1, 1) for sy in (-1, 1)])
+    assert np.allclose(sorted(map(tuple, m["p"])), exp, atol=1e-12)
+    # tangent basis: t1 = world X for a horizontal contact
+    assert np.allclose(m["t1"], [1, 0, 0])
+
+
+def test_ground_manifold_flat_and_on_edge():
+    hx, hy, hz = HALF
+    pen = 3e-5
+    g = oracle.ground_manifold([0.01, 0.02, hz - pen], [1, 0, 0, 0], HALF)
+    assert g["np"] == 4 and np.allclose(g["depth"], pen, atol=1e-14)
+    assert np.allclose(sorted(map(tuple, g["p"])),
+                       sorted([(0.01 + sx * hx, 0.02 + sy * hy, -pen / 2) for sx in (-1, 1) for sy in (-1, 1)]), atol=1e-13)
+    # standing on its long edge: rotated 45 deg about body x -> 2 points at x = +-hx
+    q = qaxis((1, 0, 0), math.pi / 4)
+    zc = (hy + hz) / math.sqrt(2) - pen
+    e = oracle.ground_manifold([0, 0, zc], q, HALF)
+    assert e["np"] == 2
+    assert np.allclose(sorted(e["p"][:, 0]), [-hx, hx], atol=1e-12)
+    assert np.allclose(e["depth"], pen, atol=1e-12)
+
+
+def test_edge_edge_contact_single_point():
+    hx, hy, hz = HALF
+    qa = qaxis((1, 0, 0), math.pi / 4)                       # top edge along world x
+    qb = qmul(qaxis((0, 1, 0), math.pi / 4), qaxis((0, 0, 1), math.pi / 2))  # long axis along y, bottom edge along y
+    ext = (hy + hz) / math.sqrt(2)
+    pen = 1e-4
+    xa = np.array([0.0, 0.0, 0.0])
+    xb = np.array([0.004, -0.006, 2 * ext - pen])
+    m = oracle.pair_manifold(xa, qa, HALF, xb, qb, HALF)
+    assert m["axis"] >= 6 and m["np"] == 1
+    assert np.allclose(m["n"], [0, 0, 1], atol=1e-12)
+    assert abs(m["depth"][0] - pen) < 1e-12
+    # midpoint of the closest points of the crossing edges: A's top edge runs
+    # along world x, B's bottom edge along world y
+    def corners(x, q):
+        R = oracle.rotmat(q)
+        return np.array([x + R @ (np.array([sx, sy, sz]) * HALF)
+                         for sx in (-1, 1) for sy in (-1, 1) for sz in (-1, 1)])
+    ca, cb = corners(xa, qa), corners(xb, qb)
+    top_a = ca[np.isclose(ca[:, 2], ca[:, 2].max())]
+    bot_b = cb[np.isclose(cb[:, 2], cb[:, 2].min())]
+    assert len(top_a) == 2 and len(bot_b) == 2
+    exp = [bot_b[0, 0], top_a[0, 1], 0.5 * (top_a[0, 2] + bot_b[0, 2])]
+    assert np.allclose(m["p"][0], exp, atol=1e-12)
+
+
+# ------------------------------------------------------------ Sec. 7 friction / PGS
+@pytest.mark.parametrize("mu", [0.25, 0.4, 0.6])
+def test_incline_stick_slide(mu):
+    """Block on a plane tilted by theta (gravity rotated): sticks iff tan(theta) <= mu,
+    otherwise slides with a = g (sin theta - mu cos theta)."""
+    hz = HALF[2]
+    thc = math.atan(mu)
+    for f, slides in ((0.98, False), (1.02, True)):
+        th = f * thc
+        g = (G * math.sin(th), 0.0, -G * math.cos(th))
+        W = one_box_world((0, 0, hz), mu=mu, gravity=g, residual_tol=1e-11, pgs_iter_cap=10000)
+        n = 240
+        W.step(n)
+        x, _, v, _ = W.state()
+        if not slides:
+            assert abs(x[0, 0]) < 1e-6
+        else:
+            a = 2 * x[0, 0] / (H * H * n * (n + 1))
+            a_exp = G * (math.sin(th) - mu * math.cos(th))
+            assert abs(a - a_exp) / a_exp < 0.01, (a, a_exp)
+
+
+def test_single_block_total_normal_impulse():
+    W = one_box_world((0, 0, HALF[2]), residual_tol=1e-10, pgs_iter_cap=10000)
+    for _ in range(5):
+        W.step(1)
+        c = oracle.contact_dicts(W.contacts(0))
+        assert len(c) == 1 and c[0]["a"] == -1
+        assert abs(c[0]["lam"][:, 0].sum() - 0.015 * G * H) < 1e-12
+        # per-point friction is not unique (a self-cancelling set is allowed);
+        # the net tangential impulse and the net torque about the COM are zero
+        P = c[0]["lam"][:, 0:1] * c[0]["n"] + c[0]["lam"][:, 1:2] * c[0]["t1"] \
+            + c[0]["lam"][:, 2:3] * np.cross(c[0]["n"], c[0]["t1"])
+        x, _, _, _ = W.state()
+        assert np.abs(P[:, :2].sum(0)).max() < 1e-12
+        tau = np.cross(c[0]["p"] - x[:, 0], P).sum(0)
+        assert np.abs(tau).max() < 1e-12
+
+
+def test_two_block_frictionless_stack_lcp():
+    """Block 1 on the ground, block 2 on block 1, mu = 0: the LCP's unique pair
+    totals are (m1 + m2) g h at the ground and m2 g h between the blocks."""
+    hz = HALF[2]
+    m1, m2 = 0.015, 0.021
+    sc = synth.custom_scene([dict(half=HALF, x=(0, 0, hz), mass=m1, mu=0.0),
+                             dict(half=HALF, x=(0, 0, 3 * hz), q=qaxis((0, 0, 1), 0.3), mass=m2, mu=0.0)],
+                            ground_mu=0.0)
+    sc.x = sc.x.astype(float); sc.x[2] = [hz, 3 * hz]
+    sc.mass = np.array([m1, m2], float); sc.q = np.c_[[1, 0, 0, 0], qaxis((0, 0, 1), 0.3)].astype(float)
+    sc.half = np.array(HALF, float)[:, None].repeat(2, 1)
+    W = oracle.World(sc, synth.params(residual_tol=1e-12, pgs_iter_cap=20000, warm_start=0))
+    W.step(1)
+    c = {(r["a"], r["b"]): r for r in oracle.contact_dicts(W.contacts(0))}
+    assert abs(c[(-1, 0)]["lam"][:, 0].sum() - (m1 + m2) * G * H) < 1e-12
+    assert abs(c[(0, 1)]["lam"][:, 0].sum() - m2 * G * H) < 1e-12
+    _, _, v, w = W.state()
+    assert np.abs(v).max() < 1e-10 and np.abs(w).max() < 1e-9
+
+
+# ------------------------------------------------------------- Sec. 5 Ziglar
+def golden_thresholds():
+    rows = []
+    with open(os.path.join(os.path.dirname(__file__), "golden", "ziglar_thresholds.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                mu, k, F = line.split()
+                rows.append((float(mu), float(k), float(F)))
+    return rows
+
+
+@pytest.mark.parametrize("mu,k,F_mN", golden_thresholds())
+def test_push_force_reproduces_printed_thresholds(mu, k, F_mN):
+    """The schedule's push force F = factor k mu_s m g (factor 1) on a 19.6 g block
+    reproduces Tab. ziglar / Tab. results to the printed 0.1 mN."""
+    m = 0.0196
+    W = one_box_world((0, 0, 3.0), mass=m, mu=mu)
+    prot = synth._protocol([[(0, synth.AXIS_Y, 1.0, 1.0, k, 0, 1, 0)]], 1)
+    W.set_protocol(prot)
+    W.run_protocol(max_steps=1)
+    _, _, v, _ = W.state()
+    F = m * v[0, 0] / H
+    assert abs(F * 1e3 - F_mN) <= 0.05 + 1e-9, (F * 1e3, F_mN)
+
+
+def ziglar_rig(mu, factor, steps=120):
+    """Determinate Y-axis rig: B on the ground, T on B (same footprint), a static
+    frictionless stop S against T's +x end face, clear of B.  Pushing B along its
+    long axis, ground friction mu 2mg and T friction mu mg resist: B slides iff
+    F > 3 mu m g."""
+    hx, hy, hz = HALF
+    m = 0.015
+    sx = 0.005
+    s_bot = 4 * hz - (2 * hz + 3e-3)
+    boxes = [dict(half=HALF, x=(0, 0, hz), mass=m, mu=mu),
+             dict(half=HALF, x=(0, 0, 3 * hz), mass=m, mu=mu),
+             dict(half=(sx, hy, s_bot / 2), x=(hx + sx, 0, 2 * hz + 3e-3 + s_bot / 2), mass=0.0, mu=0.0)]
+    sc = synth.custom_scene(boxes, ground_mu=mu)
+    for key in ("half", "x", "q", "v", "w", "mass", "mu", "ground_mu"):
+        setattr(sc, key, getattr(sc, key).astype(float))
+    sc.half[:, 2] = (sx, hy, s_bot / 2)
+    sc.x[:, 0] = (0, 0, hz); sc.x[:, 1] = (0, 0, 3 * hz); sc.x[:, 2] = (hx + sx, 0, 2 * hz + 3e-3 + s_bot / 2)
+    sc.half[:, 0] = HALF; sc.half[:, 1] = HALF; sc.mass[:] = (m, m, 0.0); sc.mu[:] = (mu, mu, 0.0)
+    W = oracle.World(sc, synth.params(residual_tol=1e-9, pgs_iter_cap=20000))
+    W.apply_push(0, 0, synth.AXIS_Y, factor * 3 * mu * m * G, steps)
+    W.step(steps)
+    x, _, _, _ = W.state()
+    return x[0, 0], x[0, 1]
+
+
+@pytest.mark.parametrize("mu", [0.25, 0.40, 0.60])
+def test_ziglar_y_threshold_located_within_2pct(mu):
+    xb, xt = ziglar_rig(mu, 0.98)
+    assert abs(xb) < 1e-3 and abs(xt) < 1e-3
+    xb, xt = ziglar_rig(mu, 1.02)
+    assert xb > 1e-3 and abs(xt) < 1e-3
+
+
+# ------------------------------------------------------------ Sec. 8 stability
+def test_support_margin_square_and_degenerate():
+    sq = np.array([[0, 0], [2, 0], [2, 2], [0, 2], [1, 1]], float)
+    assert abs(oracle.support_margin(sq, [1.0, 1.0]) - 1.0) < 1e-15
+    assert abs(oracle.support_margin(sq, [1.5, 1.0]) - 0.5) < 1e-15
+    assert abs(oracle.support_margin(sq, [2.5, 1.0]) + 0.5) < 1e-15
+    seg = np.array([[0, 0], [2, 0], [1, 0]], float)
+    assert abs(oracle.support_margin(seg, [1.0, 1.0]) + 1.0) < 1e-15
+
+
+def test_com_imbalance_single_block_and_tower_base():
+    W = one_box_world((0.0, 0.0, HALF[2]))
+    assert abs(W.com_imbalance(0) + HALF[1]) < 1e-12       # footprint L x W, COM centred
+    sc = synth.build_scene([synth.Tower(levels=4)], 0)
+    Wt = oracle.World(sc, synth.params())
+    # bottom layer: three blocks side by side = a 3W x L square (L = 3W), the
+    # jittered masses move the COM off the centre
+    m = sc.mass.astype(float)
+    cx, cy = (sc.x[0] * m).sum() / m.sum(), (sc.x[1] * m).sum() / m.sum()
+    d = min(1.5 * 0.025 - abs(cx), 1.5 * 0.025 - abs(cy))
+    assert abs(Wt.com_imbalance(0) + d) < 1e-9
+
+
+@pytest.mark.slow
+def test_resting_tower_18_levels_two_seconds():
+    """Resting 18-level tower over 2 s (480 steps): max penetration < 1e-5 m and
+    max point speed < 1e-4 m/s."""
+    sc = synth.build_scene([synth.Tower()], 0)
+    W = oracle.World(sc, synth.params(residual_tol=1e-6, pgs_iter_cap=50000))
+    maxpen = maxspeed = 0.0
+    half = sc.half.astype(float)
+    for s in range(480):
+        W.step(1)
+        _, _, v, w = W.state()
+        c = oracle.contact_dicts(W.contacts(0))
+        maxpen = max(maxpen, max(r["depth"].max() for r in c))
+        sp = np.sqrt((v ** 2).sum(0)) + np.sqrt((w ** 2).sum(0)) * np.sqrt((half ** 2).sum(0))
+        maxspeed = max(maxspeed, sp.max())
+    assert maxpen < 1e-5, maxpen
+    assert maxspeed < 1e-4, maxspeed
