@@ -33,6 +33,10 @@
 #define EDGE_REL 0.05   /* reading: cross axis must beat the face axis by 5% */
 #define CROSS_EPS 1e-6  /* reading: skip degenerate cross axes */
 #define INC_TIE 1e-9    /* reading: incident-face choice hysteresis */
+#define CLIP_EPS 1e-6   /* reading: the reference face is enlarged by 1 um for clipping */
+#define MERGE_EPS 1e-6  /* reading: clipped vertices closer than 1 um are one vertex */
+#define DEPTH_TIE 1e-6  /* reading: depths within 1 um tie (lowest index wins) */
+#define AREA_TIE 1e-9   /* reading: squared distances / areas within 1e-9 m^2 tie */
 #define OR_PI 3.14159265358979323846
 
 typedef struct {
@@ -233,36 +237,44 @@ static double hull4_area(const double* a, const double* b, const double* c, cons
 }
 
 /* Reading of "sample up to 4 points": (1) deepest, (2) farthest from (1),
-   (3) largest triangle with (1),(2), (4) largest added hull area; lowest index
-   wins ties; output in that order.  Applied only when more than 4 remain. */
+   (3) largest triangle with (1),(2), (4) largest added hull area; scores within
+   a tie tolerance count as equal and the lowest index wins; output in that
+   order.  Applied only when more than 4 remain. */
 static int reduce4(int n, double P[][3], double* D, const double* nrm, int* sel) {
   if (n <= 4) { for (int i = 0; i < n; ++i) sel[i] = i; return n; }
   int used[8] = {0};
+  /* each pick: the first index whose score is within the tie tolerance of the best */
+  double dmax = D[0];
+  for (int i = 1; i < n; ++i) if (D[i] > dmax) dmax = D[i];
   int i1 = 0;
-  for (int i = 1; i < n; ++i) if (D[i] > D[i1]) i1 = i;
+  while (D[i1] < dmax - DEPTH_TIE) ++i1;
   used[i1] = 1;
-  int i2 = -1; double best = -1;
+  double sc[8], best;
+  best = -1;
   for (int i = 0; i < n; ++i) {
-    if (used[i]) continue;
     double d[3] = {P[i][0] - P[i1][0], P[i][1] - P[i1][1], P[i][2] - P[i1][2]};
-    double s = dot3(d, d);
-    if (s > best) { best = s; i2 = i; }
+    sc[i] = used[i] ? -1 : dot3(d, d);
+    if (sc[i] > best) best = sc[i];
   }
+  int i2 = 0;
+  while (used[i2] || sc[i2] < best - AREA_TIE) ++i2;
   used[i2] = 1;
-  int i3 = -1; best = -1;
+  best = -1;
   for (int i = 0; i < n; ++i) {
-    if (used[i]) continue;
-    double s = tri_area(P[i1], P[i2], P[i], nrm);
-    if (s > best) { best = s; i3 = i; }
+    sc[i] = used[i] ? -1 : tri_area(P[i1], P[i2], P[i], nrm);
+    if (sc[i] > best) best = sc[i];
   }
+  int i3 = 0;
+  while (used[i3] || sc[i3] < best - AREA_TIE) ++i3;
   used[i3] = 1;
   double base = tri_area(P[i1], P[i2], P[i3], nrm);
-  int i4 = -1; best = -1;
+  best = -1;
   for (int i = 0; i < n; ++i) {
-    if (used[i]) continue;
-    double s = hull4_area(P[i1], P[i2], P[i3], P[i], nrm) - base;
-    if (s > best) { best = s; i4 = i; }
+    sc[i] = used[i] ? -1 : hull4_area(P[i1], P[i2], P[i3], P[i], nrm) - base;
+    if (sc[i] > best) best = sc[i];
   }
+  int i4 = 0;
+  while (used[i4] || sc[i4] < best - AREA_TIE) ++i4;
   sel[0] = i1; sel[1] = i2; sel[2] = i3; sel[3] = i4;
   return 4;
 }
@@ -297,9 +309,11 @@ static int finish_points(or_pair* pr, int n, double P[][3], double* D, const dou
 /* Face-face manifold.  Reading of steps a-d: the reference face is the face of
    the SAT-axis owner whose outward normal is along the contact direction, the
    incident face is the other box's face most anti-parallel to it; the incident
-   quad is clipped by the reference face's four side planes; per-point depth is
-   the distance below the reference face; points with depth > -margin are kept;
-   the contact point is the midpoint between the incident point and the face. */
+   quad is clipped by the reference face's four side planes (the face enlarged
+   by CLIP_EPS, so edges lying on a side plane, as in a flush tower, are not
+   split by rounding); per-point depth is the distance below the reference
+   face; points with depth > -margin are kept, coincident ones once; the
+   contact point is the midpoint between the incident point and the face. */
 static int face_manifold(const box_t* A, const box_t* B, int axis, const double* n, double margin, or_pair* pr) {
   const box_t *ref, *inc;
   int ra;
@@ -335,20 +349,26 @@ static int face_manifold(const box_t* A, const box_t* B, int axis, const double*
     for (int k = 0; k < 3; ++k)
       a.p[i][k] = ci[k] + s1[i] * inc->h[j1] * v1[k] + s2[i] * inc->h[j2] * v2[k];
   double mu1[3] = {-u1[0], -u1[1], -u1[2]}, mu2[3] = {-u2[0], -u2[1], -u2[2]};
-  clip_plane(&a, &b, cr, u1, ref->h[r1]);
-  clip_plane(&b, &a, cr, mu1, ref->h[r1]);
-  clip_plane(&a, &b, cr, u2, ref->h[r2]);
-  clip_plane(&b, &a, cr, mu2, ref->h[r2]);
+  clip_plane(&a, &b, cr, u1, ref->h[r1] + CLIP_EPS);
+  clip_plane(&b, &a, cr, mu1, ref->h[r1] + CLIP_EPS);
+  clip_plane(&a, &b, cr, u2, ref->h[r2] + CLIP_EPS);
+  clip_plane(&b, &a, cr, mu2, ref->h[r2] + CLIP_EPS);
   double P[8][3], D[8];
   int m = 0;
   for (int i = 0; i < a.n; ++i) {
     double rel[3] = {cr[0] - a.p[i][0], cr[1] - a.p[i][1], cr[2] - a.p[i][2]};
     double dep = dot3(rel, nref);
-    if (dep > -margin) {
-      for (int k = 0; k < 3; ++k) P[m][k] = a.p[i][k] + 0.5 * dep * nref[k];
-      D[m] = dep;
-      ++m;
+    if (!(dep > -margin)) continue;
+    int dup = 0;
+    for (int j = 0; j < m && !dup; ++j) {
+      double q[3] = {a.p[i][0] - (P[j][0] - 0.5 * D[j] * nref[0]), a.p[i][1] - (P[j][1] - 0.5 * D[j] * nref[1]),
+                     a.p[i][2] - (P[j][2] - 0.5 * D[j] * nref[2])};
+      dup = dot3(q, q) < MERGE_EPS * MERGE_EPS;
     }
+    if (dup) continue;
+    for (int k = 0; k < 3; ++k) P[m][k] = a.p[i][k] + 0.5 * dep * nref[k];
+    D[m] = dep;
+    ++m;
   }
   pr->ref_face = 2 * ra + (sr > 0 ? 0 : 1) + (axis < 3 ? 0 : 8);
   pr->inc_face = 2 * ji + (si > 0 ? 0 : 1);

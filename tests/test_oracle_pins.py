@@ -236,7 +236,9 @@ def test_manifold_crossed_blocks_square():
     qb = qaxis((0, 0, 1), math.pi / 2)
     m = oracle.pair_manifold(np.zeros(3), [1, 0, 0, 0], HALF, [0.003, -0.002, 2 * hz - pen], qb, HALF)
     assert m["np"] == 4 and m["axis"] == 2
-    exp = sorted([(0.003 + sx * hy, sy * hy, hz - pen / 2) for sx in (-1, 1) for sy in (-1, 1)])
+    # B's long edges are clipped by A's side planes y = +-hy, taken 1 um outward
+    # (the clipping tolerance); B's own edges give x = 0.003 +- hy
+    exp = sorted([(0.003 + sx * hy, sy * (hy + 1e-6), hz - pen / 2) for sx in (-1, 1) for sy in (-1, 1)])
     assert np.allclose(sorted(map(tuple, m["p"])), exp, atol=1e-12)
     # tangent basis: t1 = world X for a horizontal contact
     assert np.allclose(m["t1"], [1, 0, 0])
@@ -441,3 +443,29 @@ def test_resting_tower_18_levels_two_seconds():
         maxspeed = max(maxspeed, sp.max())
     assert maxpen < 1e-5, maxpen
     assert maxspeed < 1e-4, maxspeed
+
+
+def test_flush_tower_manifolds_are_exact_rectangles():
+    """Flush 18-level tower (single-precision quaternions of the 90 degree layers):
+    each crossing pair touches in a W x W square, each side-by-side pair in an
+    L x H face, each ground pair in the L x W footprint; 4 points each, no
+    vertex split by rounding on the side planes."""
+    sc = synth.build_scene([synth.Tower()], 0)
+    W = oracle.World(sc, synth.params(pgs_iters=1))
+    W.step(1)
+    L, Wd, Hh = 0.075, 0.025, 0.015
+    n_cross = n_side = n_ground = 0
+    for r in oracle.contact_dicts(W.contacts(0)):
+        assert r["np"] == 4
+        p = r["p"]
+        ext = np.sort(p.max(0) - p.min(0))
+        if r["a"] < 0:
+            n_ground += 1
+            assert np.allclose(ext, [0, Wd, L], atol=3e-6)
+        elif r["a"] // 3 == r["b"] // 3:
+            n_side += 1
+            assert np.allclose(ext, [0, Hh, L], atol=3e-6)
+        else:
+            n_cross += 1
+            assert np.allclose(ext, [0, Wd, Wd], atol=3e-6)
+    assert (n_ground, n_side, n_cross) == (3, 36, 153)
