@@ -1,0 +1,304 @@
+"""Benchmark: body-steps/s of the batched block-tower step on GB300.
+
+Workload: the 450-episode, three-friction removal-round batch (150 episodes at
+each mu_s in {0.25, 0.40, 0.60}, 18-level towers of 0.075 x 0.025 x 0.015 m
+blocks, 15 g +- 2 %, 1..8 removals of non-top blocks pushed along block X or Y
+at U[0.8, 1.5] x the Ziglar threshold, 0.5 s push + 1 s settle each), solved in
+residual mode (PGS residual <= 1e-5 m/s), dt = 1/240 s, plain PGS with
+previous-frame warm start.  Synthetic, seeded inputs stand in for the paper's
+episode data.
+
+One bench step = the whole job: every episode run through its schedule to the
+end in one persistent launch (jb_run_protocol).  value = body-steps of all
+episodes / device time; e2e = the same through the C ABI from host buffers
+(batch upload, schedule upload, run, statistics readback) timed on the host.
+
+--impl reference times the FP64 CPU oracle on the host cores instead, on a
+bounded sample of the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+# algorithmic flops per unit of work (FMA = 2): PGS row work per contact point
+# per sweep, contact setup per point, SAT + manifold per kept pair, AABB test
+# per candidate pair, integration per body
+FLOP_POINT_SWEEP = 162.0
+FLOP_POINT_SETUP = 180.0
+FLOP_PAIR = 750.0
+FLOP_BP = 12.0
+FLOP_BODY = 60.0
+SMS, FP32_LANES = 152, 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--episodes", type=int, default=0, help="use the first n episodes (0 = all 450)")
+    ap.add_argument("--max-steps", type=int, default=1 << 30, help="cap physics steps per episode")
+    ap.add_argument("--tol", type=float, default=1e-5)
+    ap.add_argument("--cap", type=int, default=20000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-episodes", type=int, default=0)
+    ap.add_argument("--cpu-steps", type=int, default=30)
+    return ap.parse_args()
+
+
+def workload(args, rank):
+    scene, prot, prm = synth.friction_workload(seed=1 + rank)
+    if args.episodes:
+        # spread the subset over the three friction levels
+        E = scene.n_episodes
+        idx = np.linspace(0, E - 1, args.episodes).round().astype(int)
+        scene, prot = synth.subset(scene, prot, idx)
+    prm = dict(prm, residual_tol=args.tol, pgs_iter_cap=args.cap)
+    return scene, prot, prm
+
+
+def algorithmic_flops(st):
+    return (FLOP_POINT_SWEEP * st["point_sweeps"].sum() + FLOP_POINT_SETUP * st["point_steps"].sum()
+            + FLOP_PAIR * st["pair_steps"].sum() + FLOP_BP * st["bp_tests"].sum()
+            + FLOP_BODY * st["body_steps"].sum())
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,utilization.gpu,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.rows = []
+        if self.proc is None:
+            return False
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+        return False
+
+    def summary(self):
+        if not getattr(self, "rows", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        num = lambda s: float(s) if s.replace(".", "", 1).isdigit() else float("nan")
+        load = [r for r in self.rows if num(r[2]) > 0] or self.rows
+        sm = [num(r[0]) for r in load]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": num(self.rows[0][1]), "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+def cpu_baseline(args, scene, prot, prm):
+    """FP64 oracle on the host cores, on a bounded sample of the same workload:
+    the first `cpu_steps` steps of `cpu_episodes` episodes spread over the batch."""
+    import oracle
+    ncores = oracle.num_threads()
+    ne = args.cpu_episodes or ncores
+    idx = np.linspace(0, scene.n_episodes - 1, ne).round().astype(int)
+    s, p = synth.subset(scene, prot, idx)
+    s64 = synth.Scene(s.body_off, *[getattr(s, k).astype(np.float64) for k in
+                                    ("half", "mass", "mu", "x", "q", "v", "w", "ground_mu")])
+    w = oracle.World(s64, prm)
+    w.set_protocol(p)
+    t0 = time.perf_counter()
+    w.run_protocol(max_steps=args.cpu_steps, threads=ncores)
+    dt = time.perf_counter() - t0
+    st = w.stats()
+    bs = float(st["body_steps"].sum())
+    return {"value": bs / dt, "unit": "body-steps/s", "cores": ncores, "kind": "oracle",
+            "sample": f"first {args.cpu_steps} steps of {ne} of the {scene.n_episodes} episodes "
+                      f"(evenly spaced over the three mu levels), FP64, OpenMP over episodes",
+            "seconds": dt, "sweeps_per_solve": float(st["total_sweeps"].sum() / max(st["solves"].sum(), 1))}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    scene, prot, prm = workload(args, 0)
+    vals = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(args, scene, prot, prm)
+        if i >= args.warmup:
+            vals.append(cb)
+    v = statistics.mean(c["value"] for c in vals)
+    line = {"impl": "reference", "metric": "body-steps/s at PGS residual <= 1e-5 (plain PGS)",
+            "value": v, "unit": "body-steps/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(c["seconds"] for c in vals),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "450 episodes x 18-level towers, mu {0.25,0.40,0.60}, removal rounds",
+                       "residual_tol": args.tol, "sample": vals[0]["sample"]},
+            "cpu_baseline": {k: vals[0][k] for k in ("kind", "cores", "sample")} | {"value": v, "unit": "body-steps/s"},
+            "e2e": {"value": v, "unit": "body-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+    import paper_2606_28394_gb300 as jb
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    scene, prot, prm = workload(args, rank)
+    M = int(prot.off[-1])
+    stream = torch.cuda.current_stream(dev)
+    batch = jb.Batch(scene, prm, max_moves=M, stream=stream, device=dev)
+    batch.set_protocol(prot)
+    snap = batch.workspace.clone()          # resident initial state (schedule started)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
+
+    def reset():
+        batch.workspace.copy_(snap)
+
+    def one_step():
+        reset()
+        flush.fill_(1)
+        torch.cuda.synchronize(dev)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        batch.run_protocol(args.max_steps)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        return e0.elapsed_time(e1)
+
+    for _ in range(args.warmup):
+        one_step()
+    with Clocks(local) as clk:
+        times = [one_step() for _ in range(args.steps)]
+    st = batch.stats()
+    ms = float(sum(times))
+    body_steps = float(st["body_steps"].sum())
+    flops = algorithmic_flops(st)
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    tot = torch.tensor([body_steps * args.steps], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+    ms_max = float(t.item())
+    value = float(tot.item()) / (ms_max / 1e3)
+
+    # end to end through the C ABI from host buffers: create (upload scene),
+    # set schedule (upload), run, read statistics back
+    e2e = None
+    if not args.no_e2e:
+        e2e_times = []
+        h2d = (scene.body_off.nbytes + scene.half.nbytes + scene.mass.nbytes + scene.mu.nbytes
+               + scene.x.nbytes + scene.q.nbytes + scene.v.nbytes + scene.w.nbytes + scene.ground_mu.nbytes
+               + sum(getattr(prot, f).nbytes for f in ("off", "block", "axis", "sign", "factor", "k",
+                                                        "remove", "push_steps", "settle_steps")))
+        d2h = scene.n_episodes * jb.C.sizeof(jb.jb_episode_stats)
+        for _ in range(max(1, args.steps)):
+            flush.fill_(1)
+            torch.cuda.synchronize(dev)
+            barrier()
+            t0 = time.perf_counter()
+            b2 = jb.Batch(scene, prm, max_moves=M, stream=stream, device=dev)
+            b2.set_protocol(prot)
+            b2.run_protocol(args.max_steps)
+            s2 = b2.stats()
+            torch.cuda.synchronize(dev)
+            e2e_times.append(time.perf_counter() - t0)
+            del b2
+        et = torch.tensor([sum(e2e_times)], device=dev, dtype=torch.float64)
+        if world > 1:
+            dist.all_reduce(et, op=dist.ReduceOp.MAX)
+        e2e = {"value": float(tot.item()) / float(et.item()) * len(e2e_times) / max(args.steps, 1),
+               "unit": "body-steps/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "note": "host wall clock, includes batch upload from pageable host arrays"}
+        assert float(s2["body_steps"].sum()) == body_steps
+
+    peaks = load_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tf = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    achieved = flops / (ms / args.steps / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
+            "frac": achieved / peak_tf, "traffic": None,
+            "peak_note": f"FP32 FMA peak: {SMS} SMs x {FP32_LANES} lanes x 2 flop x {sm_max:.0f} MHz (max SM clock of measured)",
+            "kernel": "episode_kernel (persistent, one warp per episode)",
+            "flops_per_launch": flops}
+    line = {"metric": "body-steps/s at PGS residual <= 1e-5 (plain PGS, previous-frame warm start)",
+            "value": value, "unit": "body-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "450 episodes x 18-level towers, mu {0.25,0.40,0.60} x 150, removal rounds"
+                       if not args.episodes else f"{args.episodes} of the 450 episodes",
+                       "residual_tol": args.tol, "pgs_iter_cap": args.cap, "max_steps": args.max_steps,
+                       "l2": "flushed (256 MB write) before every timed step",
+                       "episodes": scene.n_episodes, "bodies": scene.n_bodies},
+            "roofline": roof, "gpu_launches": args.steps, "clocks": clk.summary(),
+            "e2e": e2e,
+            "solver": {"sweeps_per_solve": float(st["total_sweeps"].sum() / max(st["solves"].sum(), 1)),
+                       "not_converged_episodes": int(((st["status"] & jb.JB_EP_NOT_CONVERGED) != 0).sum()),
+                       "collapsed": int(st["collapsed"].sum()), "body_steps_per_job": body_steps,
+                       "max_colours": int(st["max_colours"].max())}}
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(args, scene, prot, prm)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,260 @@
+/*
+ * jb.h -- C ABI of the batched rigid-body step for block-tower collapse
+ * episodes ("GPU-Accelerated Inverse Structural Anastylosis from Block
+ * Collapse Dynamics").
+ *
+ * One call advances thousands of independent episodes (towers of boxes on a
+ * ground plane) through the paper's step: AABB broadphase (Sec. 6.1,
+ * Eq. aabb), OBB separating-axis narrowphase over 15 axes (Sec. 6.2),
+ * face-clipped contact manifolds (Sec. 6.2.1), a Projected Gauss-Seidel
+ * normal + Coulomb-friction solve (Sec. 7, Eq. keff, Eq. lambda_n,
+ * Eq. coulomb_pgs), semi-implicit Euler with quaternion integration
+ * (Sec. 4, Eq. newton_euler, Eq. quat_int), Baumgarte position correction
+ * (Sec. 7.4, Eq. baumgarte) and the stability / collapse tests of Sec. 8
+ * (Eq. stability, Eq. collapse).  Pushes follow Ziglar's thresholds
+ * F = k mu_s m g (Sec. 5, Eq. 4 and Eq. 8).
+ *
+ * Conventions
+ *  - SI units, z up, the ground is the plane z = 0 (a static body).
+ *  - Quaternions q = [w, x, y, z] (Hamilton product), unit length; angular
+ *    velocity in the world frame.  Body frame of a block: x = length,
+ *    y = width, z = thickness.
+ *  - Per-body arrays are structure-of-arrays, component-major: the c-th
+ *    component of body b (global index over all episodes) is arr[c * B + b].
+ *    Episodes are concatenated; body_off[e] .. body_off[e+1]-1 are episode
+ *    e's bodies and "block" arguments are episode-local indices.
+ *  - Memory: the library never allocates device memory.  The caller passes
+ *    one device workspace (jb_workspace_bytes) that the batch carves up; all
+ *    other pointers are host pointers unless a call says otherwise.  The
+ *    library never frees caller memory.
+ *  - Work is queued on the stream given at creation; calls that return data
+ *    to host memory synchronise that stream before returning.
+ *  - Errors: every call returns a jb_status.  Argument errors are detected
+ *    synchronously and nothing is launched.  Device-side failures (contact
+ *    capacity exceeded, sweep cap hit, non-finite state) are recorded per
+ *    episode and surfaced by jb_sync / jb_read_episode_stats.  The message of
+ *    the last error on the calling thread is returned by jb_last_error().
+ */
+#ifndef JB_H
+#define JB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t jb_status;
+#define JB_OK 0
+#define JB_EINVAL (-1)   /* bad argument (null pointer, bad size, bad parameter) */
+#define JB_ENOMEM (-2)   /* workspace too small */
+#define JB_ECUDA (-3)    /* a CUDA runtime call failed */
+#define JB_ERANGE (-4)   /* episode or block index out of range */
+#define JB_ESTATE (-5)   /* call not valid in the batch's current state */
+
+/* per-episode status bits (jb_episode_stats.status) */
+#define JB_EP_CONTACT_OVERFLOW 1  /* more pairs or candidates than the capacity; extras dropped */
+#define JB_EP_NOT_CONVERGED 2     /* residual mode hit pgs_iter_cap at least once */
+#define JB_EP_NONFINITE 4         /* a position or velocity became NaN/Inf; episode stopped */
+#define JB_EP_TOO_MANY_COLOURS 8  /* colouring overflowed; overflow pairs solved serially */
+
+/* episode phases */
+#define JB_PH_FREE 0     /* host-driven (jb_step) */
+#define JB_PH_PUSH 1
+#define JB_PH_SETTLE 2
+#define JB_PH_REST 3     /* collapsed; running until at rest (Sec. 8.3) */
+#define JB_PH_DONE 4
+
+/* push axes (block-local, Sec. 5): X = width axis (body y), Y = long axis (body x) */
+#define JB_AXIS_X 0
+#define JB_AXIS_Y 1
+
+/* Solver parameters.  Defaults (jb_default_params) follow the paper's
+ * Appendix A table where it gives a value: dt = 1/240 s, e = 0.10,
+ * beta = 0.35, slop = 0.4 mm, AABB eps = 2 mm, g = 9.81. */
+typedef struct {
+  float dt;                 /* step length, s */
+  int32_t n_sub;            /* substeps per step (each a full detect-solve-integrate) */
+  int32_t pgs_iters;        /* sweeps per solve in fixed mode (residual_tol == 0) */
+  float residual_tol;       /* > 0: residual mode, sweep until residual <= tol (m/s) */
+  int32_t pgs_iter_cap;     /* sweep cap in residual mode */
+  int32_t pgs_min_iters;    /* sweeps before the first residual check */
+  int32_t residual_every;   /* residual mode: check every this many sweeps (>= 1) */
+  float restitution;        /* e, applied as (1+e) in the normal row (Sec. 7.1) */
+  float beta, slop;         /* Eq. baumgarte */
+  float contact_margin;     /* speculative contact margin m_c, m */
+  float aabb_eps;           /* Eq. aabb epsilon, m */
+  float gravity[3];         /* m/s^2 */
+  int32_t warm_start;       /* 0 none, 1 previous-frame impulses */
+  float match_radius;       /* warm-start point match radius, m */
+  float fall_frac;          /* Eq. collapse f_d */
+  float collapse_ek;        /* Eq. collapse eps_k, J */
+  float collapse_theta_deg; /* Eq. collapse theta_th, degrees */
+  float rest_ek;            /* Sec. 8.3 rest threshold, J */
+  int32_t rest_steps;       /* Sec. 8.3 step budget after collapse */
+} jb_solver_params;
+
+/* Initial scene: host arrays, B = body_off[n_episodes] bodies. */
+typedef struct {
+  int32_t n_episodes;
+  const int32_t* body_off;  /* [E+1], body_off[0] = 0, non-decreasing */
+  const float* half;        /* [3][B] half extents, > 0 */
+  const float* mass;        /* [B] kg; 0 marks a static box */
+  const float* mu;          /* [B] Coulomb coefficient; a pair uses the smaller of its two */
+  const float* x;           /* [3][B] centre of mass */
+  const float* q;           /* [4][B] orientation (normalised on load) */
+  const float* v;           /* [3][B] linear velocity, may be NULL (zero) */
+  const float* w;           /* [3][B] angular velocity, may be NULL (zero) */
+  const float* ground_mu;   /* [E] ground friction coefficient */
+} jb_scene;
+
+/* Tower description (Sec. 3.1: 3 blocks per layer, alternating perpendicular
+ * layers, flush, bottom on z = 0; even 0-based levels along world X). */
+typedef struct {
+  int32_t levels;
+  int32_t per_level;        /* blocks per level (3 in the paper) */
+  float dims[3];            /* block length, width, thickness, m */
+  float mass;               /* nominal block mass, kg */
+  float mass_jitter;        /* uniform +- fraction (SplitMix64 draw per block) */
+  float mu_s;
+} jb_tower_desc;
+
+/* Per-episode push/removal schedule, CSR over moves (host arrays).  Move m
+ * pushes `block` along its `axis` with force sign * factor * k * mu_s * m * |g|
+ * (Sec. 5 threshold times a factor) at its centre of mass for push_steps
+ * steps, then deletes the block if remove != 0, then lets the tower settle for
+ * settle_steps steps.  The episode stops early on collapse (Eq. collapse) and
+ * then runs until at rest (Sec. 8.3). */
+typedef struct {
+  const int32_t* off;        /* [E+1] */
+  const int32_t* block;      /* [M] episode-local body index */
+  const int32_t* axis;       /* [M] JB_AXIS_X / JB_AXIS_Y */
+  const float* sign;         /* [M] +1 / -1 */
+  const float* factor;       /* [M] */
+  const float* k;            /* [M] threshold multiplier (3 or 4 in Sec. 5) */
+  const int32_t* remove;     /* [M] */
+  const int32_t* push_steps; /* [M] */
+  const int32_t* settle_steps; /* [M] */
+} jb_protocol;
+
+/* One contact point as read back: pair (a, b) with a = -1 for the ground,
+ * SAT axis id (0..2 faces of a, 3..5 faces of b, 6..14 edge pairs a_i x b_j,
+ * 15 ground), reference/incident feature ids, the point, the normal (from a
+ * to b), the depth (positive = penetrating) and the accumulated impulses
+ * (normal, t1, t2) of the last solve. */
+typedef struct {
+  int32_t a, b, axis, ref_face, inc_face, point;
+  float p[3];
+  float n[3];
+  float t1[3];
+  float depth;
+  float lambda[3];
+} jb_contact;
+
+typedef struct {
+  int32_t status;           /* JB_EP_* bits */
+  int32_t phase;            /* JB_PH_* */
+  int32_t collapsed;        /* Eq. collapse fired */
+  int32_t resting;          /* kinetic energy below rest_ek */
+  int32_t n_fallen;         /* active blocks displaced more than fall_frac * length */
+  int32_t moves_done;
+  int32_t n_pairs, n_points;  /* of the last substep */
+  int32_t last_sweeps;
+  int32_t steps;
+  int32_t max_colours;      /* most colours used by one solve (Gauss-Seidel phases per sweep) */
+  int32_t reserved;
+  float com_imbalance;      /* minus the support-polygon margin of Eq. stability, m */
+  float kinetic;            /* J, active dynamic bodies */
+  float last_residual;      /* m/s */
+  float max_residual;       /* m/s, over all solves */
+  double total_sweeps;
+  double solves;
+  double body_steps;        /* sum over steps of active dynamic bodies */
+  /* work counters (sums over substeps): contact points x sweeps, contact
+     points, contact pairs, broadphase pair tests */
+  double point_sweeps, point_steps, pair_steps, bp_tests;
+} jb_episode_stats;
+
+typedef struct jb_batch jb_batch;
+
+void jb_default_params(jb_solver_params* p);
+
+/* Tower builder (host only, no device work).  jb_tower_layout writes the
+ * CSR body offsets [E+1]; jb_tower_init fills half, mass, mu, x, q for all
+ * bodies ([3][B], [B], [B], [3][B], [4][B]) and ground_mu [E].  Mass draws:
+ * u = splitmix64(seed ^ e*0x9E3779B97F4A7C15 ^ (1<<48) ^ block) >> 11 scaled
+ * to [0,1), m = mass * (1 + mass_jitter * (2u - 1)). */
+jb_status jb_tower_layout(const jb_tower_desc* towers, int32_t n_episodes, int32_t* body_off);
+jb_status jb_tower_init(const jb_tower_desc* towers, int32_t n_episodes, uint64_t seed,
+                        const int32_t* body_off, float* half, float* mass, float* mu,
+                        float* x, float* q, float* ground_mu);
+
+/* Device workspace needed for a batch with these episode sizes (host body_off)
+ * and at most max_moves scheduled moves in total.  Returns 0 on bad input. */
+size_t jb_workspace_bytes(int32_t n_episodes, const int32_t* body_off,
+                          const jb_solver_params* p, int32_t max_moves);
+
+/* Creates a batch over caller-owned device workspace d_workspace (at least
+ * jb_workspace_bytes, 256-byte aligned), uploads the scene and initialises
+ * derived state on `cuda_stream` (a cudaStream_t, NULL = legacy default).
+ * The batch starts in the host-driven phase with an empty contact cache. */
+jb_status jb_batch_create(const jb_scene* scene, const jb_solver_params* p, int32_t max_moves,
+                          void* d_workspace, size_t workspace_bytes, void* cuda_stream,
+                          jb_batch** out);
+void jb_batch_destroy(jb_batch* b);   /* frees the host handle only */
+
+/* Replaces the solver parameters (same batch shape). */
+jb_status jb_set_params(jb_batch* b, const jb_solver_params* p);
+
+/* Uploads a schedule (total moves <= max_moves) and starts move 0 of every
+ * episode (episodes with no moves are marked done). */
+jb_status jb_set_protocol(jb_batch* b, const jb_protocol* prot);
+/* Runs every unfinished episode through its schedule for at most max_steps
+ * steps in one persistent launch.  Asynchronous. */
+jb_status jb_run_protocol(jb_batch* b, int32_t max_steps);
+
+/* Host-driven stepping.  jb_apply_push: for n entries, constant force
+ * force_N (signed) along the block's axis (direction fixed at the call) for
+ * n_steps steps.  jb_remove_block deactivates blocks.  jb_step advances all
+ * episodes in the host-driven phase by n_steps steps.  Asynchronous. */
+jb_status jb_apply_push(jb_batch* b, int32_t n, const int32_t* episode, const int32_t* block,
+                        const int32_t* axis, const float* force_N, const int32_t* n_steps);
+jb_status jb_remove_block(jb_batch* b, int32_t n, const int32_t* episode, const int32_t* block);
+jb_status jb_step(jb_batch* b, int32_t n_steps);
+
+/* Waits for queued work; *n_bad_episodes (may be NULL) = episodes whose status is non-zero. */
+jb_status jb_sync(jb_batch* b, int32_t* n_bad_episodes);
+
+/* State transfer, [3][B] / [4][B] arrays, host pointers unless device_ptrs != 0
+ * (then device pointers, copied on the batch stream).  Any pointer may be NULL.
+ * jb_write_state keeps the contact cache unless clear_cache != 0 and, when
+ * reset_reference != 0, takes the new poses as the collapse reference. */
+jb_status jb_read_state(jb_batch* b, float* x, float* q, float* v, float* w, int32_t device_ptrs);
+jb_status jb_write_state(jb_batch* b, const float* x, const float* q, const float* v,
+                         const float* w, int32_t device_ptrs, int32_t clear_cache,
+                         int32_t reset_reference);
+/* Active flags [B] (1 = in the simulation). */
+jb_status jb_read_active(jb_batch* b, int32_t* active);
+
+/* Contact points of the last substep of one episode, natural order (ground
+ * pairs by body, then pairs (a, b) ascending, points in manifold order). */
+jb_status jb_read_contacts(jb_batch* b, int32_t episode, jb_contact* out, int32_t cap,
+                           int32_t* n_out);
+/* Per-episode statistics [E]; computes the support-polygon margin on the device. */
+jb_status jb_read_episode_stats(jb_batch* b, jb_episode_stats* out);
+
+/* Raw snapshot of all mutable device state (bodies, episode state, contact
+ * caches, schedule) for exact resume.  jb_state_bytes gives the size. */
+size_t jb_state_bytes(const jb_batch* b);
+jb_status jb_save_state(jb_batch* b, void* host_buf, size_t bytes);
+jb_status jb_load_state(jb_batch* b, const void* host_buf, size_t bytes);
+
+const char* jb_status_str(jb_status s);
+const char* jb_last_error(void);
+const char* jb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,135 @@
+// Internal layout of a batch on the device: the descriptor every kernel
+// receives by value, the per-episode state record and the shared-memory plan
+// of one episode (one warp).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/jb.h"
+
+namespace jbk {
+
+constexpr int kWarpsPerCta = 1;          // one warp (episode) per CTA
+constexpr int kMaxColours = 64;          // colour kSerial is solved by one lane
+constexpr int kSerial = kMaxColours - 1;
+constexpr int kMaxPts = 4;               // points per pair (Sec. 6.2.1, step d)
+constexpr int kNatPtFloats = 12;         // p[3], depth, local[3], lambda[3], pad[2]
+constexpr int kNatPairFloats = 8;        // n[3], depth_max, t1[3], mu
+constexpr int kSrtPairFloats = 8;        // n[3], t1[3], mu, depth_max
+constexpr int kSrtPtFloats = 10;         // p[3], invk[3], bias, lambda[3]
+
+// body flags
+constexpr int kActive = 1;
+constexpr int kStatic = 2;
+
+// launch modes of the episode kernel
+constexpr int kModeFree = 0;
+constexpr int kModeProtocol = 1;
+
+// Pair capacity of an episode with nb bodies.  An intact tower needs about
+// 3.6 pairs per body; piles after a collapse need more.
+__host__ __device__ inline int pair_capacity(int nb) { return 8 * nb + 16; }
+// Broadphase candidate capacity (shared memory, u32 per candidate).
+__host__ __device__ inline int cand_capacity(int nb) { return 16 * nb + 64; }
+
+struct EpState {
+  int32_t phase, mi, remaining, pb, rest_left;
+  int32_t collapsed, resting, status;
+  int32_t cur, npairs, ncolours, npoints;
+  int32_t last_sweeps, steps, n_fallen, max_colours;
+  float last_res, max_res, kinetic, com_imb;
+  double total_sweeps, solves, body_steps;
+  double point_sweeps, point_steps, pair_steps, bp_tests;
+};
+
+struct Params {
+  float dt;
+  int n_sub, pgs_iters;
+  float residual_tol;
+  int pgs_iter_cap, pgs_min_iters, residual_every;
+  float restitution, beta, slop, contact_margin, aabb_eps;
+  float g[3];
+  int warm_start;
+  float match_radius, fall_frac, collapse_ek, collapse_cos, rest_ek;
+  int rest_steps;
+};
+
+// One contact buffer (the batch holds two: this step's and the previous one).
+// "Natural" arrays are indexed by the pair's position in natural order;
+// "sorted" arrays by its slot in colour order.  Per-episode regions start at
+// pair_off[e] (pairs) and 4 * pair_off[e] (points).
+struct ContactBuf {
+  uint32_t* nat_key;    // ((a + 1) << 16) | b, a = -1 for the ground
+  uint32_t* nat_feat;   // axis | ref_face << 8 | inc_face << 16 | np << 24
+  uint32_t* nat_slot;   // slot | colour << 16
+  float* nat_pt;        // [P * 4][kNatPtFloats]; lambda = final impulses of the step
+  float* nat_pf;        // [P][kNatPairFloats]
+  // colour-sorted solver arrays, used when a step's pairs exceed the
+  // shared-memory capacity (stride Pc per field)
+  float* srt_f;         // per episode: [kSrtPairFloats][Pc]
+  uint32_t* srt_ab;     // local a | local b << 16 (ground = nb)
+  int32_t* srt_np;
+  float* srt_pt;        // per episode: [kSrtPtFloats * 4][Pc]
+};
+
+struct Dev {
+  int E, B, nb_max, pc_max;
+  const int32_t* body_off;
+  const int64_t* pair_off;
+  // bodies
+  float *x, *q, *v, *w, *half, *mass, *invm, *invI, *mu, *x0, *z0, *f;
+  int32_t *flags, *f_steps;
+  const float* ground_mu;
+  EpState* ep;
+  // schedule
+  int32_t *mv_off, *mv_block, *mv_axis, *mv_remove, *mv_push, *mv_settle;
+  float *mv_sign, *mv_factor, *mv_k;
+  ContactBuf buf[2];
+  int32_t* work_counter;
+  const int32_t* order;   // episode processing order [E]
+  Params P;
+  int smem_per_warp;      // bytes
+  int ps;                 // pairs whose solver arrays fit in shared memory
+};
+
+// Shared-memory plan of one episode (bytes from the warp's base).
+struct SmemPlan {
+  int nbs;                // body slots (nb_max + 1, the last one is the ground)
+  int off_f;              // float arrays
+  int off_flags;
+  int off_mask;
+  int off_cand;
+  int off_col;
+  int off_sf, off_ab, off_np, off_sp;   // colour-sorted solver arrays (ps pairs)
+  int bytes;
+};
+
+constexpr int kBodyFloats = 36;  // x3 q4 v3 w3 half3 R9 Iw6 ext3 invm mu
+
+// Pairs of an episode whose solver arrays are kept in shared memory: an
+// intact tower needs about 3.6 per body.
+__host__ __device__ inline int smem_pairs(int nb_max, int pc_max) {
+  int p = (9 * nb_max) / 2 + 16;
+  return p < pc_max ? p : pc_max;
+}
+
+__host__ __device__ inline SmemPlan smem_plan(int nb_max, int pc_max, int ps) {
+  SmemPlan s;
+  s.nbs = nb_max + 1;
+  int o = 0;
+  s.off_mask = o; o += 8 * s.nbs;
+  s.off_f = o; o += 4 * kBodyFloats * s.nbs;
+  s.off_flags = o; o += 4 * s.nbs;
+  s.off_cand = o; o += 4 * cand_capacity(nb_max);
+  s.off_col = o; o += 4 * 3 * (kMaxColours + 1);
+  o = (o + 15) & ~15;
+  s.off_sf = o; o += 4 * kSrtPairFloats * ps;
+  s.off_ab = o; o += 4 * ps;
+  s.off_np = o; o += 4 * ps;
+  s.off_sp = o; o += 4 * kSrtPtFloats * kMaxPts * ps;
+  o = (o + 15) & ~15;
+  s.bytes = o;
+  return s;
+}
+
+}  // namespace jbk

@@ -1,0 +1,1434 @@
+// Device kernels of the batched rigid-body step (sm_103a).
+//
+// One warp owns one episode (a tower) for the whole launch: the episode's
+// bodies live in shared memory, its contact pairs and points in an L1/L2
+// resident global workspace.  A persistent grid claims episodes from a work
+// counter.  Per substep the warp runs (paper sections in brackets):
+//   forces and frames [Sec. 4.2, Eq. rotmat]
+//   broadphase, all pairs, ballot compaction in natural order [Sec. 6.1, Eq. aabb]
+//   SAT over 15 axes + face-clipped manifold, one pair per lane [Sec. 6.2, 6.2.1]
+//   warm-start matching against the previous step's contacts
+//   greedy edge colouring of the contact graph (colours persist across steps)
+//   contact setup [Sec. 7.1, Eq. keff]
+//   coloured projected Gauss-Seidel: pairs of one colour share no dynamic body
+//   and run in parallel, colours in sequence [Sec. 7.1-7.3, Eq. lambda_n,
+//   Eq. coulomb_pgs]; residual mode sweeps until the residual <= tol
+//   integration [Sec. 4.2, Eq. quat_int] and position correction [Eq. baumgarte]
+//   collapse / rest bookkeeping and the push schedule [Sec. 5, Sec. 8]
+// Everything is FP32.  Waits are warp barriers only; every loop is bounded.
+#include <cfloat>
+#include <cstdint>
+
+#include "jb_internal.cuh"
+
+namespace jbk {
+
+#define FULL 0xffffffffu
+
+// ------------------------------------------------------------ float3 helpers
+__device__ __forceinline__ float3 f3(float a, float b, float c) { return make_float3(a, b, c); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator-(float3 a) { return f3(-a.x, -a.y, -a.z); }
+__device__ __forceinline__ float3 operator*(float s, float3 a) { return f3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross(float3 a, float3 b) {
+  return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float sgnf(float v) { return v >= 0.f ? 1.f : -1.f; }
+
+// ------------------------------------------------------ shared-memory view
+enum { FX = 0, FQ = 3, FV = 7, FW = 10, FH = 13, FR = 16, FI = 25, FE = 31, FM = 34, FMU = 35 };
+
+struct Sm {
+  int nbs;
+  float* F;
+  int* flags;
+  unsigned long long* mask;
+  uint32_t* cand;
+  int* cnt;   // [kMaxColours + 1]
+  int* off;   // [kMaxColours + 1]
+  int* run;   // [kMaxColours + 1]
+  float* sf;  // colour-sorted solver arrays for up to ps pairs
+  uint32_t* ab;
+  int32_t* np;
+  float* sp;
+  int ps;
+  __device__ __forceinline__ float& at(int f, int i) const { return F[f * nbs + i]; }
+  __device__ __forceinline__ float3 ld3(int f, int i) const { return f3(at(f, i), at(f + 1, i), at(f + 2, i)); }
+  __device__ __forceinline__ void st3(int f, int i, float3 v) const { at(f, i) = v.x; at(f + 1, i) = v.y; at(f + 2, i) = v.z; }
+  // column k of the rotation matrix (body axis k in world coordinates)
+  __device__ __forceinline__ float3 axis(int i, int k) const { return f3(at(FR + k, i), at(FR + 3 + k, i), at(FR + 6 + k, i)); }
+  __device__ __forceinline__ float3 iw_mul(int i, float3 u) const {
+    float xx = at(FI, i), yy = at(FI + 1, i), zz = at(FI + 2, i), xy = at(FI + 3, i), xz = at(FI + 4, i), yz = at(FI + 5, i);
+    return f3(xx * u.x + xy * u.y + xz * u.z, xy * u.x + yy * u.y + yz * u.z, xz * u.x + yz * u.y + zz * u.z);
+  }
+};
+
+__device__ __forceinline__ Sm sm_view(unsigned char* base, int nb_max, int pc_max, int ps) {
+  SmemPlan p = smem_plan(nb_max, pc_max, ps);
+  Sm s;
+  s.nbs = p.nbs;
+  s.mask = reinterpret_cast<unsigned long long*>(base + p.off_mask);
+  s.F = reinterpret_cast<float*>(base + p.off_f);
+  s.flags = reinterpret_cast<int*>(base + p.off_flags);
+  s.cand = reinterpret_cast<uint32_t*>(base + p.off_cand);
+  s.cnt = reinterpret_cast<int*>(base + p.off_col);
+  s.off = s.cnt + (kMaxColours + 1);
+  s.run = s.off + (kMaxColours + 1);
+  s.sf = reinterpret_cast<float*>(base + p.off_sf);
+  s.ab = reinterpret_cast<uint32_t*>(base + p.off_ab);
+  s.np = reinterpret_cast<int32_t*>(base + p.off_np);
+  s.sp = reinterpret_cast<float*>(base + p.off_sp);
+  s.ps = ps;
+  return s;
+}
+
+// ------------------------------------------------------------ narrowphase
+struct Box {
+  float3 c, a0, a1, a2, h;
+  __device__ __forceinline__ float3 ax(int k) const { return k == 0 ? a0 : (k == 1 ? a1 : a2); }
+  __device__ __forceinline__ float hk(int k) const { return k == 0 ? h.x : (k == 1 ? h.y : h.z); }
+  __device__ __forceinline__ float radius(float3 u) const {
+    return h.x * fabsf(dot(a0, u)) + h.y * fabsf(dot(a1, u)) + h.z * fabsf(dot(a2, u));
+  }
+};
+
+__device__ __forceinline__ Box box_of(const Sm& s, int i) {
+  Box b;
+  b.c = s.ld3(FX, i);
+  b.a0 = s.axis(i, 0); b.a1 = s.axis(i, 1); b.a2 = s.axis(i, 2);
+  b.h = s.ld3(FH, i);
+  return b;
+}
+
+struct Contact {
+  int axis, ref_face, inc_face, np;
+  float3 n;
+  float delta, dmax;
+  float3 p[kMaxPts];
+  float depth[kMaxPts];
+};
+
+constexpr float kTieAbs = 1e-7f;    // SAT axis hysteresis (m)
+constexpr float kEdgeRel = 0.05f;   // a cross axis must beat the best face axis by 5 %
+constexpr float kCrossEps = 1e-6f;  // degenerate cross axes are skipped
+constexpr float kIncTie = 1e-9f;
+constexpr float kClipEps = 1e-6f;   // reference face enlarged by 1 um for clipping
+constexpr float kMergeEps = 1e-6f;  // clipped vertices closer than 1 um are one vertex
+constexpr float kDepthTie = 1e-6f;  // depths within 1 um tie (lowest index wins)
+constexpr float kAreaTie = 1e-9f;   // squared distances / areas within 1e-9 m^2 tie
+
+__device__ __forceinline__ float3 sat_axis(const Box& A, const Box& B, int k, bool& ok) {
+  ok = true;
+  if (k < 3) return A.ax(k);
+  if (k < 6) return B.ax(k - 3);
+  float3 u = cross(A.ax((k - 6) / 3), B.ax((k - 6) % 3));
+  float l = sqrtf(dot(u, u));
+  if (l < kCrossEps) { ok = false; return f3(0.f, 0.f, 0.f); }
+  return (1.f / l) * u;
+}
+
+__device__ __forceinline__ float tri_area(float3 a, float3 b, float3 c, float3 n) {
+  return 0.5f * fabsf(dot(cross(b - a, c - a), n));
+}
+__device__ __forceinline__ float quad_area(float3 a, float3 b, float3 c, float3 d, float3 n) {
+  float3 s = cross(a, b) + cross(b, c) + cross(c, d) + cross(d, a);
+  return 0.5f * fabsf(dot(s, n));
+}
+__device__ float hull4(float3 a, float3 b, float3 c, float3 d, float3 n) {
+  float m = quad_area(a, b, c, d, n);
+  m = fmaxf(m, quad_area(a, b, d, c, n));
+  m = fmaxf(m, quad_area(a, c, b, d, n));
+  m = fmaxf(m, tri_area(a, b, c, n));
+  m = fmaxf(m, tri_area(a, b, d, n));
+  m = fmaxf(m, tri_area(a, c, d, n));
+  m = fmaxf(m, tri_area(b, c, d, n));
+  return m;
+}
+
+// Keeps at most 4 of m points: deepest; farthest from it; largest triangle;
+// largest added hull area, in that order.  Scores within a tie tolerance count
+// as equal and the lowest index wins.
+__device__ void keep4(int m, const float3* P, const float* D, float3 nrm, Contact& C) {
+  if (m <= kMaxPts) {
+    float dm = -FLT_MAX;
+    for (int i = 0; i < m; ++i) { C.p[i] = P[i]; C.depth[i] = D[i]; dm = fmaxf(dm, D[i]); }
+    C.np = m; C.dmax = dm;
+    return;
+  }
+  float sc[8];
+  unsigned used = 0;
+  float best = -FLT_MAX;
+  for (int i = 0; i < m; ++i) best = fmaxf(best, D[i]);
+  int i1 = 0;
+  while (D[i1] < best - kDepthTie) ++i1;
+  used |= 1u << i1;
+  best = -1.f;
+  for (int i = 0; i < m; ++i) {
+    float3 d = P[i] - P[i1];
+    sc[i] = (used >> i & 1) ? -1.f : dot(d, d);
+    best = fmaxf(best, sc[i]);
+  }
+  int i2 = 0;
+  while ((used >> i2 & 1) || sc[i2] < best - kAreaTie) ++i2;
+  used |= 1u << i2;
+  best = -1.f;
+  for (int i = 0; i < m; ++i) {
+    sc[i] = (used >> i & 1) ? -1.f : tri_area(P[i1], P[i2], P[i], nrm);
+    best = fmaxf(best, sc[i]);
+  }
+  int i3 = 0;
+  while ((used >> i3 & 1) || sc[i3] < best - kAreaTie) ++i3;
+  used |= 1u << i3;
+  float base = tri_area(P[i1], P[i2], P[i3], nrm);
+  best = -1.f;
+  for (int i = 0; i < m; ++i) {
+    sc[i] = (used >> i & 1) ? -1.f : hull4(P[i1], P[i2], P[i3], P[i], nrm) - base;
+    best = fmaxf(best, sc[i]);
+  }
+  int i4 = 0;
+  while ((used >> i4 & 1) || sc[i4] < best - kAreaTie) ++i4;
+  int sel[4] = {i1, i2, i3, i4};
+  float dm = -FLT_MAX;
+  for (int q = 0; q < 4; ++q) { C.p[q] = P[sel[q]]; C.depth[q] = D[sel[q]]; dm = fmaxf(dm, D[sel[q]]); }
+  C.np = 4; C.dmax = dm;
+}
+
+// Sutherland-Hodgman against the half-space (p - c).u <= h.
+__device__ int clip_poly(const float3* in, int n, float3* out, float3 c, float3 u, float h) {
+  int m = 0;
+  if (n == 0) return 0;
+  float3 S = in[n - 1];
+  float dS = dot(S - c, u) - h;
+  for (int i = 0; i < n; ++i) {
+    float3 E = in[i];
+    float dE = dot(E - c, u) - h;
+    if (dE <= 0.f) {
+      if (dS > 0.f && m < 8) { out[m++] = S + (dS / (dS - dE)) * (E - S); }
+      if (m < 8) out[m++] = E;
+    } else if (dS <= 0.f && m < 8) {
+      out[m++] = S + (dS / (dS - dE)) * (E - S);
+    }
+    S = E; dS = dE;
+  }
+  return m;
+}
+
+// Clipping runs in coordinates relative to the reference box centre, which
+// keeps FP32 rounding of the clip intersections small for boxes far from the
+// origin; the points are moved back at the end.
+__device__ void face_contact(const Box& A, const Box& B, int axis, float3 n, float margin, Contact& C) {
+  Box ref = axis < 3 ? A : B;
+  Box inc = axis < 3 ? B : A;
+  const float3 origin = ref.c;
+  inc.c = inc.c - origin;
+  ref.c = f3(0.f, 0.f, 0.f);
+  int ra = axis < 3 ? axis : axis - 3;
+  float3 nref = axis < 3 ? n : -n;
+  float3 ax = ref.ax(ra);
+  float sr = sgnf(dot(ax, nref));
+  float3 cr = ref.c + (sr * ref.hk(ra)) * ax;
+  int r1 = (ra + 1) % 3, r2 = (ra + 2) % 3;
+  float3 u1 = ref.ax(r1), u2 = ref.ax(r2);
+  float h1 = ref.hk(r1), h2 = ref.hk(r2);
+  int ji = 0; float bd = -1.f;
+  for (int j = 0; j < 3; ++j) {
+    float dd = fabsf(dot(inc.ax(j), nref));
+    if (dd > bd + kIncTie) { bd = dd; ji = j; }
+  }
+  float3 bj = inc.ax(ji);
+  float si = -sgnf(dot(bj, nref));
+  float3 ci = inc.c + (si * inc.hk(ji)) * bj;
+  int j1 = (ji + 1) % 3, j2 = (ji + 2) % 3;
+  float3 v1 = inc.hk(j1) * inc.ax(j1), v2 = inc.hk(j2) * inc.ax(j2);
+  float3 pa[8], pb[8];
+  pa[0] = ci + v1 + v2; pa[1] = ci - v1 + v2; pa[2] = ci - v1 - v2; pa[3] = ci + v1 - v2;
+  int m = clip_poly(pa, 4, pb, cr, u1, h1 + kClipEps);
+  m = clip_poly(pb, m, pa, cr, -u1, h1 + kClipEps);
+  m = clip_poly(pa, m, pb, cr, u2, h2 + kClipEps);
+  m = clip_poly(pb, m, pa, cr, -u2, h2 + kClipEps);
+  float D[8];
+  int k = 0;
+  for (int i = 0; i < m; ++i) {
+    float dep = dot(cr - pa[i], nref);
+    if (!(dep > -margin)) continue;
+    bool dup = false;
+    for (int j = 0; j < k && !dup; ++j) {
+      float3 q = pa[i] - (pb[j] - (0.5f * D[j]) * nref);
+      dup = dot(q, q) < kMergeEps * kMergeEps;
+    }
+    if (dup) continue;
+    pb[k] = pa[i] + (0.5f * dep) * nref; D[k] = dep; ++k;
+  }
+  C.ref_face = 2 * ra + (sr > 0.f ? 0 : 1) + (axis < 3 ? 0 : 8);
+  C.inc_face = 2 * ji + (si > 0.f ? 0 : 1);
+  keep4(k, pb, D, n, C);
+  for (int i = 0; i < C.np; ++i) C.p[i] = C.p[i] + origin;
+}
+
+__device__ void edge_contact(const Box& A, const Box& B, int axis, float3 n, float delta, Contact& C) {
+  int i = (axis - 6) / 3, j = (axis - 6) % 3;
+  float3 pa = f3(0.f, 0.f, 0.f), pb = B.c - A.c;   // relative to A's centre
+  for (int m = 0; m < 3; ++m) {
+    if (m != i) { float3 c = A.ax(m); pa = pa + (sgnf(dot(c, n)) * A.hk(m)) * c; }
+    if (m != j) { float3 c = B.ax(m); pb = pb + (-sgnf(dot(c, n)) * B.hk(m)) * c; }
+  }
+  float3 ea = A.ax(i), eb = B.ax(j);
+  float3 r = pa - pb;
+  float bb = dot(ea, eb), c = dot(ea, r), f = dot(eb, r);
+  float den = 1.f - bb * bb;
+  float s = den > 1e-12f ? (bb * f - c) / den : 0.f;
+  s = fminf(fmaxf(s, -A.hk(i)), A.hk(i));
+  float t = fminf(fmaxf(f + s * bb, -B.hk(j)), B.hk(j));
+  C.p[0] = 0.5f * ((pa + s * ea) + (pb + t * eb)) + A.c;
+  C.depth[0] = delta;
+  C.dmax = delta;
+  C.np = 1;
+  C.ref_face = 16 + i;
+  C.inc_face = 16 + j;
+}
+
+// SAT over the 15 axes; on contact (min delta > -margin) builds the manifold.
+__device__ bool box_box(const Box& A, const Box& B, float margin, Contact& C) {
+  float3 d = B.c - A.c;
+  float delta[15];
+  bool valid[15];
+  float dmin = FLT_MAX;
+#pragma unroll
+  for (int k = 0; k < 15; ++k) {
+    bool ok;
+    float3 u = sat_axis(A, B, k, ok);
+    valid[k] = ok;
+    delta[k] = ok ? A.radius(u) + B.radius(u) - fabsf(dot(d, u)) : 0.f;
+    if (ok) dmin = fminf(dmin, delta[k]);
+  }
+  if (!(dmin > -margin)) return false;
+  int bf = 0;
+#pragma unroll
+  for (int k = 1; k < 6; ++k) if (delta[k] < delta[bf] - kTieAbs) bf = k;
+  int be = -1;
+  float dbe = 0.f;
+#pragma unroll
+  for (int k = 6; k < 15; ++k)
+    if (valid[k] && (be < 0 || delta[k] < dbe - kTieAbs)) { be = k; dbe = delta[k]; }
+  float dbf = 0.f;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) if (k == bf) dbf = delta[k];
+  int axis = (be >= 0 && dbe < dbf - (kEdgeRel * fabsf(dbf) + kTieAbs)) ? be : bf;
+  bool ok;
+  float3 n = sat_axis(A, B, axis, ok);
+  if (dot(n, d) < 0.f) n = -n;
+  C.axis = axis;
+  C.n = n;
+  C.delta = axis == be ? dbe : dbf;
+  if (axis < 6) face_contact(A, B, axis, n, margin, C);
+  else edge_contact(A, B, axis, n, C.delta, C);
+  return C.np > 0;
+}
+
+// Ground plane z = 0 as body a: corners below the margin, n = +z.
+__device__ bool ground_contact(const Box& B, float margin, Contact& C) {
+  float3 P[8];
+  float D[8];
+  int m = 0;
+  for (int c = 0; c < 8; ++c) {
+    float s0 = (c & 1) ? 1.f : -1.f, s1 = (c & 2) ? 1.f : -1.f, s2 = (c & 4) ? 1.f : -1.f;
+    float3 p = B.c + (s0 * B.h.x) * B.a0 + (s1 * B.h.y) * B.a1 + (s2 * B.h.z) * B.a2;
+    if (p.z < margin) { D[m] = -p.z; P[m] = f3(p.x, p.y, p.z + 0.5f * D[m]); ++m; }
+  }
+  if (m == 0) return false;
+  C.n = f3(0.f, 0.f, 1.f);
+  C.axis = 15; C.ref_face = 0; C.inc_face = 0;
+  keep4(m, P, D, C.n, C);
+  C.delta = C.dmax;
+  return true;
+}
+
+__device__ __forceinline__ void tangent_basis(float3 n, float3& t1, float3& t2) {
+  float3 e = fabsf(n.x) > 0.9f ? f3(0.f, 1.f, 0.f) : f3(1.f, 0.f, 0.f);
+  float3 t = e - dot(e, n) * n;
+  t1 = rsqrtf(dot(t, t)) * t;
+  t2 = cross(n, t1);
+}
+
+// ------------------------------------------------------------ warp helpers
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(FULL, v, o));
+  return v;
+}
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(FULL, v, o));
+  return v;
+}
+__device__ __forceinline__ unsigned lanemask_lt(int lane) { return (1u << lane) - 1u; }
+
+// ------------------------------------------------------------ episode view
+struct Ep {
+  int e, b0, nb, Pc, lane;
+  int64_t poff;
+  Sm s;
+};
+
+struct BufView {
+  uint32_t *key, *feat, *slot;
+  float *pt, *pf;
+  // colour-sorted solver arrays: shared memory when the step's pairs fit,
+  // else this buffer's global copy; field f of slot s at [f * stride + s]
+  uint32_t* ab;
+  int32_t* np;
+  float *sf, *sp;
+  int stride;
+};
+
+__device__ __forceinline__ BufView buf_view(const Dev& D, int which, const Ep& E) {
+  const ContactBuf& b = D.buf[which];
+  BufView v;
+  v.key = b.nat_key + E.poff;
+  v.feat = b.nat_feat + E.poff;
+  v.slot = b.nat_slot + E.poff;
+  v.pt = b.nat_pt + E.poff * kMaxPts * kNatPtFloats;
+  v.pf = b.nat_pf + E.poff * kNatPairFloats;
+  v.ab = b.srt_ab + E.poff;
+  v.np = b.srt_np + E.poff;
+  v.sf = b.srt_f + E.poff * kSrtPairFloats;
+  v.sp = b.srt_pt + E.poff * kMaxPts * kSrtPtFloats;
+  v.stride = E.Pc;
+  return v;
+}
+
+__device__ __forceinline__ void use_smem_solver(BufView& v, const Sm& s) {
+  v.ab = s.ab; v.np = s.np; v.sf = s.sf; v.sp = s.sp; v.stride = s.ps;
+}
+
+// ---------------------------------------------------------- PGS pair kernels
+// Everything a pair pass touches is loaded once into registers: the two
+// bodies' velocities, inverse masses and world inverse inertia (symmetric, 6
+// floats), the pair's frame and friction coefficient, and its points' lever
+// arms, inverse effective masses, biases and impulses.
+struct Sym3 { float xx, yy, zz, xy, xz, yz; };
+__device__ __forceinline__ float3 mul(const Sym3& I, float3 u) {
+  return f3(I.xx * u.x + I.xy * u.y + I.xz * u.z, I.xy * u.x + I.yy * u.y + I.yz * u.z,
+            I.xz * u.x + I.yz * u.y + I.zz * u.z);
+}
+__device__ __forceinline__ Sym3 ld_iw(const Sm& s, int i) {
+  Sym3 I;
+  I.xx = s.at(FI, i); I.yy = s.at(FI + 1, i); I.zz = s.at(FI + 2, i);
+  I.xy = s.at(FI + 3, i); I.xz = s.at(FI + 4, i); I.yz = s.at(FI + 5, i);
+  return I;
+}
+
+struct PairRegs {
+  int a, b, np;
+  bool da, db;
+  float3 va, wa, vb, wb, xa, xb, n, t1, t2;
+  float ima, imb, mu;
+  Sym3 Ia, Ib;
+  float3 rA[kMaxPts], rB[kMaxPts];
+  float ik[kMaxPts][3], bias[kMaxPts], lam[kMaxPts][3];
+};
+
+#define SP(f, k) B.sp[((f) * kMaxPts + (k)) * Pc + sl]
+#define SF(f) B.sf[(f) * Pc + sl]
+
+__device__ __forceinline__ void load_pair(const Sm& s, const BufView& B, int Pc, int sl, PairRegs& R) {
+  uint32_t ab = B.ab[sl];
+  R.np = B.np[sl];
+  R.a = ab & 0xffff; R.b = ab >> 16;
+  R.n = f3(SF(0), SF(1), SF(2));
+  R.t1 = f3(SF(3), SF(4), SF(5));
+  R.t2 = cross(R.n, R.t1);
+  R.mu = SF(6);
+  R.va = s.ld3(FV, R.a); R.wa = s.ld3(FW, R.a);
+  R.vb = s.ld3(FV, R.b); R.wb = s.ld3(FW, R.b);
+  R.xa = s.ld3(FX, R.a); R.xb = s.ld3(FX, R.b);
+  R.ima = s.at(FM, R.a); R.imb = s.at(FM, R.b);
+  R.Ia = ld_iw(s, R.a); R.Ib = ld_iw(s, R.b);
+  R.da = !(s.flags[R.a] & kStatic);
+  R.db = !(s.flags[R.b] & kStatic);
+}
+
+// point k: lever arms from the stored contact point, inverse effective masses,
+// bias and impulses
+__device__ __forceinline__ void load_point(const BufView& B, int Pc, int sl, int k, PairRegs& R) {
+  float3 p = f3(SP(0, k), SP(1, k), SP(2, k));
+  R.rA[k] = p - R.xa;
+  R.rB[k] = p - R.xb;
+  R.ik[k][0] = SP(3, k); R.ik[k][1] = SP(4, k); R.ik[k][2] = SP(5, k);
+  R.bias[k] = SP(6, k);
+  R.lam[k][0] = SP(7, k); R.lam[k][1] = SP(8, k); R.lam[k][2] = SP(9, k);
+}
+
+// One constraint row: impulse change dl along d at lever arms (rA, rB).
+__device__ __forceinline__ void row_apply(PairRegs& R, float3 d, float3 ia, float3 ib, float dl) {
+  R.va = R.va - (R.ima * dl) * d;
+  R.vb = R.vb + (R.imb * dl) * d;
+  R.wa = R.wa - dl * ia;
+  R.wb = R.wb + dl * ib;
+}
+
+// mode 0: apply warm-start impulses; mode 1: one Gauss-Seidel pass over the
+// pair's points, rows n, t1, t2 (Eq. lambda_n with the listing's (1+e)
+// factor, Eq. coulomb_pgs box clip with the just-updated normal impulse);
+// mode 2: position correction (Eq. baumgarte, translation only).
+template <int mode>
+__device__ __forceinline__ void pair_pass(const Sm& s, const BufView& B, int Pc, int sl, const Params& Pm) {
+  if constexpr (mode == 2) {
+    uint32_t ab = B.ab[sl];
+    int a = ab & 0xffff, b = ab >> 16;
+    float3 n = f3(SF(0), SF(1), SF(2));
+    float pen = SF(7) - Pm.slop;
+    float ima = s.at(FM, a), imb = s.at(FM, b);
+    float wsum = ima + imb;
+    if (pen > 0.f && wsum > 0.f) {
+      float c = Pm.beta * pen / wsum;
+      if (!(s.flags[a] & kStatic)) s.st3(FX, a, s.ld3(FX, a) - (c * ima) * n);
+      if (!(s.flags[b] & kStatic)) s.st3(FX, b, s.ld3(FX, b) + (c * imb) * n);
+    }
+    return;
+  }
+  PairRegs R;
+  load_pair(s, B, Pc, sl, R);
+  const float e1 = 1.f + Pm.restitution;
+#pragma unroll
+  for (int k = 0; k < kMaxPts; ++k) {
+    if (k >= R.np) break;
+    load_point(B, Pc, sl, k, R);
+    if constexpr (mode == 0) {
+      float3 Pv = R.lam[k][0] * R.n + R.lam[k][1] * R.t1 + R.lam[k][2] * R.t2;
+      R.va = R.va - R.ima * Pv;
+      R.vb = R.vb + R.imb * Pv;
+      R.wa = R.wa - mul(R.Ia, cross(R.rA[k], Pv));
+      R.wb = R.wb + mul(R.Ib, cross(R.rB[k], Pv));
+    } else {
+    const float3 rA = R.rA[k], rB = R.rB[k];
+    // the angular Jacobian terms and M^-1 J^T do not depend on the velocities
+    const float3 can = cross(rA, R.n), cbn = cross(rB, R.n);
+    const float3 ca1 = cross(rA, R.t1), cb1 = cross(rB, R.t1);
+    const float3 ca2 = cross(rA, R.t2), cb2 = cross(rB, R.t2);
+    const float3 ian = mul(R.Ia, can), ibn = mul(R.Ib, cbn);
+    const float3 ia1 = mul(R.Ia, ca1), ib1 = mul(R.Ib, cb1);
+    const float3 ia2 = mul(R.Ia, ca2), ib2 = mul(R.Ib, cb2);
+    float l0 = R.lam[k][0], l1 = R.lam[k][1], l2 = R.lam[k][2];
+    float vn = dot(R.vb - R.va, R.n) + dot(R.wb, cbn) - dot(R.wa, can);
+    float nl0 = fmaxf(0.f, l0 - e1 * (vn + R.bias[k]) * R.ik[k][0]);
+    row_apply(R, R.n, ian, ibn, nl0 - l0);
+    float lim = R.mu * nl0;
+    float v1 = dot(R.vb - R.va, R.t1) + dot(R.wb, cb1) - dot(R.wa, ca1);
+    float nl1 = fminf(fmaxf(l1 - v1 * R.ik[k][1], -lim), lim);
+    row_apply(R, R.t1, ia1, ib1, nl1 - l1);
+    float v2 = dot(R.vb - R.va, R.t2) + dot(R.wb, cb2) - dot(R.wa, ca2);
+    float nl2 = fminf(fmaxf(l2 - v2 * R.ik[k][2], -lim), lim);
+    row_apply(R, R.t2, ia2, ib2, nl2 - l2);
+    SP(7, k) = nl0; SP(8, k) = nl1; SP(9, k) = nl2;
+    }
+  }
+  if (R.da) { s.st3(FV, R.a, R.va); s.st3(FW, R.a, R.wa); }
+  if (R.db) { s.st3(FV, R.b, R.vb); s.st3(FW, R.b, R.wb); }
+}
+
+// Residual of one pair at the current state (no update): max over rows of
+// k |proj(lambda - (v + b) / k) - lambda|, k the inverse effective mass.
+__device__ __forceinline__ float pair_residual(const Sm& s, const BufView& B, int Pc, int sl) {
+  PairRegs R;
+  load_pair(s, B, Pc, sl, R);
+  float r = 0.f;
+#pragma unroll
+  for (int k = 0; k < kMaxPts; ++k) {
+    if (k >= R.np) break;
+    load_point(B, Pc, sl, k, R);
+    const float3 rA = R.rA[k], rB = R.rB[k];
+    float3 dv = R.vb - R.va;
+    float vn = dot(dv, R.n) + dot(R.wb, cross(rB, R.n)) - dot(R.wa, cross(rA, R.n));
+    float v1 = dot(dv, R.t1) + dot(R.wb, cross(rB, R.t1)) - dot(R.wa, cross(rA, R.t1));
+    float v2 = dot(dv, R.t2) + dot(R.wb, cross(rB, R.t2)) - dot(R.wa, cross(rA, R.t2));
+    float l0 = R.lam[k][0], l1 = R.lam[k][1], l2 = R.lam[k][2];
+    float lim = R.mu * l0;
+    float p0 = fmaxf(0.f, l0 - (vn + R.bias[k]) * R.ik[k][0]);
+    float p1 = fminf(fmaxf(l1 - v1 * R.ik[k][1], -lim), lim);
+    float p2 = fminf(fmaxf(l2 - v2 * R.ik[k][2], -lim), lim);
+    float m = fmaxf(fabsf(p0 - l0) / R.ik[k][0], fmaxf(fabsf(p1 - l1) / R.ik[k][1], fabsf(p2 - l2) / R.ik[k][2]));
+    if (!(m <= r)) r = m;   // keeps NaN
+  }
+  return r;
+}
+#undef SP
+#undef SF
+
+// Residual of the whole episode (warp max; NaN propagates).
+__device__ __noinline__ float episode_residual(const Sm& s, const BufView& B, int Pc, int npairs, int lane) {
+  float r = 0.f;
+  for (int sl = lane; sl < npairs; sl += 32) {
+    float m = pair_residual(s, B, Pc, sl);
+    if (!(m <= r)) r = m;
+  }
+  bool nan = __any_sync(FULL, !(r == r));
+  return nan ? __int_as_float(0x7fc00000) : warp_max(r);
+}
+
+// Runs `mode` over every colour in order; lanes take the slots of a colour.
+template <int mode>
+__device__ __noinline__ void colour_passes(const Sm& s, const BufView& B, int Pc, int ncol, int lane, const Params& Pm) {
+  for (int c = 0; c < ncol; ++c) {
+    int s0 = s.off[c], s1 = s.off[c + 1];
+    if (c == kSerial) {
+      if (lane == 0)
+        for (int sl = s0; sl < s1; ++sl) pair_pass<mode>(s, B, Pc, sl, Pm);
+    } else {
+      for (int sl = s0 + lane; sl < s1; sl += 32) pair_pass<mode>(s, B, Pc, sl, Pm);
+    }
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------------ substep
+struct StepOut {
+  float res;
+  int sweeps;
+  int npairs, npoints, ncol;
+  int status;
+};
+
+__device__ __forceinline__ void body_frame(const Sm& s, const Dev& D, int gi, int i) {
+  float w = s.at(FQ, i), x = s.at(FQ + 1, i), y = s.at(FQ + 2, i), z = s.at(FQ + 3, i);
+  float R[9] = {1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w),
+                2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w),
+                2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)};
+#pragma unroll
+  for (int k = 0; k < 9; ++k) s.at(FR + k, i) = R[k];
+  float i0 = 0.f, i1 = 0.f, i2 = 0.f;
+  if (gi >= 0 && !(s.flags[i] & kStatic)) { i0 = D.invI[gi]; i1 = D.invI[D.B + gi]; i2 = D.invI[2 * D.B + gi]; }
+  // I_world^-1 = R diag(invI) R^T (Sec. 4.1.2)
+  s.at(FI, i) = R[0] * R[0] * i0 + R[1] * R[1] * i1 + R[2] * R[2] * i2;
+  s.at(FI + 1, i) = R[3] * R[3] * i0 + R[4] * R[4] * i1 + R[5] * R[5] * i2;
+  s.at(FI + 2, i) = R[6] * R[6] * i0 + R[7] * R[7] * i1 + R[8] * R[8] * i2;
+  s.at(FI + 3, i) = R[0] * R[3] * i0 + R[1] * R[4] * i1 + R[2] * R[5] * i2;
+  s.at(FI + 4, i) = R[0] * R[6] * i0 + R[1] * R[7] * i1 + R[2] * R[8] * i2;
+  s.at(FI + 5, i) = R[3] * R[6] * i0 + R[4] * R[7] * i1 + R[5] * R[8] * i2;
+  float hx = s.at(FH, i), hy = s.at(FH + 1, i), hz = s.at(FH + 2, i);
+  s.at(FE, i) = fabsf(R[0]) * hx + fabsf(R[1]) * hy + fabsf(R[2]) * hz;
+  s.at(FE + 1, i) = fabsf(R[3]) * hx + fabsf(R[4]) * hy + fabsf(R[5]) * hz;
+  s.at(FE + 2, i) = fabsf(R[6]) * hx + fabsf(R[7]) * hy + fabsf(R[8]) * hz;
+}
+
+__device__ StepOut substep(const Dev& D, const Ep& E, EpState& st, float h) {
+  const Sm& s = E.s;
+  const Params& Pm = D.P;
+  const int lane = E.lane, nb = E.nb, Pc = E.Pc;
+  const int G = nb;   // ground slot
+  StepOut out;
+  out.status = 0;
+
+  // (1) external forces and gravity on the velocity (Sec. 4.2), frames
+  for (int i = lane; i < nb; i += 32) {
+    int gi = E.b0 + i;
+    int fl = s.flags[i];
+    if ((fl & kActive) && !(fl & kStatic)) {
+      float im = s.at(FM, i);
+      bool on = D.f_steps[gi] > 0;
+      float fx = on ? D.f[gi] : 0.f, fy = on ? D.f[D.B + gi] : 0.f, fz = on ? D.f[2 * D.B + gi] : 0.f;
+      s.at(FV, i) += h * (Pm.g[0] + fx * im);
+      s.at(FV + 1, i) += h * (Pm.g[1] + fy * im);
+      s.at(FV + 2, i) += h * (Pm.g[2] + fz * im);
+    }
+    body_frame(s, D, gi, i);
+  }
+  __syncwarp();
+
+  // (2) broadphase: ground candidates, then pairs (i, j) i < j ascending
+  int ncand = 0;
+  const int ccap = cand_capacity(nb);
+  for (int j0 = 0; j0 < nb; j0 += 32) {
+    int j = j0 + lane;
+    bool hit = false;
+    if (j < nb) {
+      int fl = s.flags[j];
+      hit = (fl & kActive) && !(fl & kStatic) && (s.at(FX + 2, j) - s.at(FE + 2, j) <= Pm.aabb_eps);
+    }
+    unsigned bal = __ballot_sync(FULL, hit);
+    int idx = ncand + __popc(bal & lanemask_lt(lane));
+    if (hit && idx < ccap) s.cand[idx] = (uint32_t)j;   // a = -1 -> key ((a+1) << 16) | b
+    ncand += __popc(bal);
+  }
+  for (int i = 0; i < nb; ++i) {
+    int fi = s.flags[i];
+    if (!(fi & kActive)) continue;
+    float xi = s.at(FX, i), yi = s.at(FX + 1, i), zi = s.at(FX + 2, i);
+    float ex = s.at(FE, i), ey = s.at(FE + 1, i), ez = s.at(FE + 2, i);
+    for (int j0 = i + 1; j0 < nb; j0 += 32) {
+      int j = j0 + lane;
+      bool hit = false;
+      if (j < nb) {
+        int fj = s.flags[j];
+        hit = (fj & kActive) && !((fi & kStatic) && (fj & kStatic)) &&
+              fabsf(xi - s.at(FX, j)) <= ex + s.at(FE, j) + Pm.aabb_eps &&
+              fabsf(yi - s.at(FX + 1, j)) <= ey + s.at(FE + 1, j) + Pm.aabb_eps &&
+              fabsf(zi - s.at(FX + 2, j)) <= ez + s.at(FE + 2, j) + Pm.aabb_eps;
+      }
+      unsigned bal = __ballot_sync(FULL, hit);
+      int idx = ncand + __popc(bal & lanemask_lt(lane));
+      if (hit && idx < ccap) s.cand[idx] = ((uint32_t)(i + 1) << 16) | (uint32_t)j;
+      ncand += __popc(bal);
+    }
+  }
+  if (ncand > ccap) { out.status |= JB_EP_CONTACT_OVERFLOW; ncand = ccap; }
+  __syncwarp();
+
+  // (3) narrowphase + manifold, one candidate per lane, natural order kept
+  const int cur = st.cur ^ 1;
+  BufView Bc = buf_view(D, cur, E);
+  BufView Bp = buf_view(D, st.cur, E);
+  int npairs = 0, npoints = 0;
+  for (int c0 = 0; c0 < ncand; c0 += 32) {
+    int c = c0 + lane;
+    bool hit = false;
+    Contact C;
+    uint32_t key = 0;
+    if (c < ncand) {
+      key = s.cand[c];
+      int a = (int)(key >> 16) - 1, b = (int)(key & 0xffff);
+      Box Bb = box_of(s, b);
+      if (a < 0) hit = ground_contact(Bb, Pm.contact_margin, C);
+      else { Box Ab = box_of(s, a); hit = box_box(Ab, Bb, Pm.contact_margin, C); }
+    }
+    unsigned bal = __ballot_sync(FULL, hit);
+    int idx = npairs + __popc(bal & lanemask_lt(lane));
+    if (idx >= Pc) hit = false;   // pair capacity: the rest is dropped and flagged
+    if (__popc(bal) + npairs > Pc) out.status |= JB_EP_CONTACT_OVERFLOW;
+    if (hit) {
+      int a = (int)(key >> 16) - 1;
+      Bc.key[idx] = key;
+      Bc.feat[idx] = (uint32_t)C.axis | ((uint32_t)C.ref_face << 8) | ((uint32_t)C.inc_face << 16) | ((uint32_t)C.np << 24);
+      int ia = a < 0 ? G : a;
+      float3 xa = s.ld3(FX, ia);
+      float3 c0v = s.axis(ia, 0), c1v = s.axis(ia, 1), c2v = s.axis(ia, 2);
+      float* pt = Bc.pt + (size_t)idx * kMaxPts * kNatPtFloats;
+      for (int k = 0; k < C.np; ++k) {
+        float3 r = C.p[k] - xa;
+        float* q = pt + k * kNatPtFloats;
+        q[0] = C.p[k].x; q[1] = C.p[k].y; q[2] = C.p[k].z; q[3] = C.depth[k];
+        q[4] = dot(c0v, r); q[5] = dot(c1v, r); q[6] = dot(c2v, r);   // R_A^T (p - x_A)
+        q[7] = 0.f; q[8] = 0.f; q[9] = 0.f;                          // warm-start impulses
+        q[10] = 0.f; q[11] = 0.f;
+      }
+      Bc.slot[idx] = 0xffffu << 16;   // no colour yet
+      float* pf = Bc.pf + (size_t)idx * kNatPairFloats;
+      pf[0] = C.n.x; pf[1] = C.n.y; pf[2] = C.n.z; pf[3] = C.dmax;
+    }
+    npairs = min(npairs + __popc(bal), Pc);
+    int pts = hit ? C.np : 0;
+    npoints += (int)warp_sum((float)pts);
+  }
+  __syncwarp();
+
+  // (4) warm-start matching and colour inheritance against the previous step
+  const int nprev = st.npairs;
+  const float mr2 = Pm.match_radius * Pm.match_radius;
+  for (int p = lane; p < npairs; p += 32) {
+    uint32_t key = Bc.key[p];
+    int lo = 0, hi = nprev - 1, q = -1;
+    while (lo <= hi) {
+      int mid = (lo + hi) >> 1;
+      uint32_t km = Bp.key[mid];
+      if (km == key) { q = mid; break; }
+      if (km < key) lo = mid + 1; else hi = mid - 1;
+    }
+    if (q < 0) continue;
+    uint32_t qs = Bp.slot[q];
+    Bc.slot[p] = (qs & 0xffff0000u);
+    if (Pm.warm_start != 1) continue;
+    uint32_t fn = Bc.feat[p], fo = Bp.feat[q];
+    if (((fn ^ fo) & 0x00ffff00u) != 0) continue;
+    int npn = fn >> 24, npo = fo >> 24;
+    float* ptn = Bc.pt + (size_t)p * kMaxPts * kNatPtFloats;
+    const float* pto = Bp.pt + (size_t)q * kMaxPts * kNatPtFloats;
+    for (int k = 0; k < npn; ++k) {
+      float* a = ptn + k * kNatPtFloats;
+      int best = -1;
+      float bd = mr2;
+      for (int j = 0; j < npo; ++j) {
+        const float* o = pto + j * kNatPtFloats;
+        float dx = o[4] - a[4], dy = o[5] - a[5], dz = o[6] - a[6];
+        float d2 = dx * dx + dy * dy + dz * dz;
+        if (d2 <= bd) { bd = d2; best = j; }
+      }
+      if (best >= 0) {   // the old point's final impulses of the previous step
+        const float* o = pto + best * kNatPtFloats;
+        a[7] = o[7]; a[8] = o[8]; a[9] = o[9];
+      }
+    }
+  }
+  __syncwarp();
+
+  // (5) colouring: inherited colours claim their bits, new pairs greedily
+  for (int i = lane; i <= nb; i += 32) s.mask[i] = 0ull;
+  __syncwarp();
+  for (int p = lane; p < npairs; p += 32) {
+    uint32_t key = Bc.key[p];
+    int col = Bc.slot[p] >> 16;
+    if (col >= kSerial) continue;
+    int a = (int)(key >> 16) - 1, b = (int)(key & 0xffff);
+    unsigned long long bit = 1ull << col;
+    if (a >= 0 && !(s.flags[a] & kStatic)) atomicOr(&s.mask[a], bit);
+    if (!(s.flags[b] & kStatic)) atomicOr(&s.mask[b], bit);
+  }
+  __syncwarp();
+  for (int p0 = 0; p0 < npairs; p0 += 32) {
+    int p = p0 + lane;
+    int col = 0, a = 0, b = 0;
+    if (p < npairs) {
+      uint32_t key = Bc.key[p];
+      col = Bc.slot[p] >> 16;
+      a = (int)(key >> 16) - 1;
+      b = (int)(key & 0xffff);
+    }
+    unsigned todo = __ballot_sync(FULL, p < npairs && col == 0xffff);
+    while (todo) {
+      int j = __ffs(todo) - 1;
+      todo &= todo - 1;
+      int aj = __shfl_sync(FULL, a, j), bj = __shfl_sync(FULL, b, j);
+      bool sa = aj < 0 || (s.flags[aj] & kStatic), sb = (s.flags[bj] & kStatic);
+      unsigned long long m = (sa ? 0ull : s.mask[aj]) | (sb ? 0ull : s.mask[bj]);
+      int c = __ffsll((long long)~m) - 1;
+      if (c < 0 || c >= kSerial) c = kSerial;
+      __syncwarp();
+      if (lane == 0 && c < kSerial) {
+        if (!sa) s.mask[aj] |= 1ull << c;
+        if (!sb) s.mask[bj] |= 1ull << c;
+      }
+      if (lane == j) col = c;
+      __syncwarp();
+    }
+    if (p < npairs) Bc.slot[p] = (uint32_t)col << 16;
+  }
+  __syncwarp();
+
+  // (6) counting sort by colour (ascending natural index within a colour)
+  for (int c = lane; c <= kMaxColours; c += 32) { s.cnt[c] = 0; s.run[c] = 0; }
+  __syncwarp();
+  for (int p = lane; p < npairs; p += 32) atomicAdd(&s.cnt[Bc.slot[p] >> 16], 1);
+  __syncwarp();
+  if (lane == 0) {
+    int acc = 0;
+    for (int c = 0; c < kMaxColours; ++c) { s.off[c] = acc; acc += s.cnt[c]; }
+    s.off[kMaxColours] = acc;
+  }
+  __syncwarp();
+  int ncol = 0;
+  {
+    int last = -1;
+    for (int c = lane; c < kMaxColours; c += 32) if (s.cnt[c] > 0) last = c;
+    ncol = (int)warp_max((float)last) + 1;
+  }
+  for (int p0 = 0; p0 < npairs; p0 += 32) {
+    int p = p0 + lane;
+    int col = p < npairs ? (int)(Bc.slot[p] >> 16) : -1 - lane;
+    unsigned grp = __match_any_sync(FULL, col);
+    int rank = __popc(grp & lanemask_lt(lane));
+    int base = 0;
+    if (p < npairs) base = s.off[col] + s.run[col];
+    __syncwarp();
+    if (p < npairs) {
+      Bc.slot[p] = ((uint32_t)col << 16) | (uint32_t)(base + rank);
+      if (rank == 0) s.run[col] += __popc(grp);
+    }
+    __syncwarp();
+  }
+
+  // (7) contact setup (Eq. keff) into the colour-sorted solver arrays:
+  // shared memory when the pairs fit, else this buffer's global copy
+  if (npairs <= s.ps) use_smem_solver(Bc, s);
+  const int S = Bc.stride;
+  const float ih = 1.f / h;
+  for (int p = lane; p < npairs; p += 32) {
+    uint32_t key = Bc.key[p];
+    int a = (int)(key >> 16) - 1, b = (int)(key & 0xffff);
+    int ia = a < 0 ? G : a;
+    int sl = Bc.slot[p] & 0xffff;
+    uint32_t ft = Bc.feat[p];
+    int np = ft >> 24;
+    const float* pt = Bc.pt + (size_t)p * kMaxPts * kNatPtFloats;
+    float* pf = Bc.pf + (size_t)p * kNatPairFloats;
+    float3 n = f3(pf[0], pf[1], pf[2]);
+    float dmax = pf[3];
+    float3 t1, t2;
+    tangent_basis(n, t1, t2);
+    float mu = fminf(s.at(FMU, ia), s.at(FMU, b));
+    pf[4] = t1.x; pf[5] = t1.y; pf[6] = t1.z; pf[7] = mu;
+    float* sf = Bc.sf;
+    float* sp = Bc.sp;
+    sf[0 * S + sl] = n.x; sf[1 * S + sl] = n.y; sf[2 * S + sl] = n.z;
+    sf[3 * S + sl] = t1.x; sf[4 * S + sl] = t1.y; sf[5 * S + sl] = t1.z;
+    sf[6 * S + sl] = mu; sf[7 * S + sl] = dmax;
+    Bc.ab[sl] = (uint32_t)ia | ((uint32_t)b << 16);
+    Bc.np[sl] = np;
+    float3 xa = s.ld3(FX, ia), xb = s.ld3(FX, b);
+    float ima = s.at(FM, ia), imb = s.at(FM, b);
+    for (int k = 0; k < np; ++k) {
+      const float* q = pt + k * kNatPtFloats;
+      float3 pp = f3(q[0], q[1], q[2]);
+      float3 rA = pp - xa, rB = pp - xb;
+      float3 dirs[3] = {n, t1, t2};
+      float ik[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        float3 ca = cross(rA, dirs[r]), cb = cross(rB, dirs[r]);
+        float kk = ima + imb + dot(ca, s.iw_mul(ia, ca)) + dot(cb, s.iw_mul(b, cb));
+        ik[r] = 1.f / kk;
+      }
+      float dep = q[3];
+      float bias = dep < 0.f ? -dep * ih : 0.f;
+#define W(f, v) sp[((f) * kMaxPts + k) * S + sl] = (v)
+      W(0, pp.x); W(1, pp.y); W(2, pp.z);
+      W(3, ik[0]); W(4, ik[1]); W(5, ik[2]); W(6, bias);
+      W(7, q[7]); W(8, q[8]); W(9, q[9]);
+#undef W
+    }
+  }
+  __syncwarp();
+
+  // (8) warm start: apply the inherited impulses
+  if (Pm.warm_start == 1) colour_passes<0>(s, Bc, S, ncol, lane, Pm);
+
+  // (9) projected Gauss-Seidel sweeps
+  int sweeps = 0;
+  float res = 0.f;
+  if (npairs > 0) {
+    const bool rmode = Pm.residual_tol > 0.f;
+    const int cap = rmode ? Pm.pgs_iter_cap : Pm.pgs_iters;
+    const int every = Pm.residual_every > 0 ? Pm.residual_every : 1;
+    while (sweeps < cap) {
+      colour_passes<1>(s, Bc, S, ncol, lane, Pm);
+      ++sweeps;
+      bool check = rmode ? (sweeps >= Pm.pgs_min_iters && ((sweeps - Pm.pgs_min_iters) % every == 0 || sweeps == cap))
+                         : (sweeps == cap);
+      if (check) {
+        res = episode_residual(s, Bc, S, npairs, lane);
+        if (rmode && (res <= Pm.residual_tol || !(res == res))) break;
+      }
+    }
+    if (rmode && sweeps >= cap && !(res <= Pm.residual_tol)) out.status |= JB_EP_NOT_CONVERGED;
+  }
+  // final impulses back to the natural arrays (warm-start cache, readback)
+  for (int p = lane; p < npairs; p += 32) {
+    int sl = Bc.slot[p] & 0xffff;
+    int np = Bc.feat[p] >> 24;
+    float* pt = Bc.pt + (size_t)p * kMaxPts * kNatPtFloats;
+    for (int k = 0; k < np; ++k) {
+      float* q = pt + k * kNatPtFloats;
+      q[7] = Bc.sp[(7 * kMaxPts + k) * S + sl];
+      q[8] = Bc.sp[(8 * kMaxPts + k) * S + sl];
+      q[9] = Bc.sp[(9 * kMaxPts + k) * S + sl];
+    }
+  }
+
+  // (10) semi-implicit position update and quaternion integration (Eq. quat_int)
+  for (int i = lane; i < nb; i += 32) {
+    int fl = s.flags[i];
+    if (!(fl & kActive) || (fl & kStatic)) continue;
+    float3 v = s.ld3(FV, i), w = s.ld3(FW, i);
+    s.st3(FX, i, s.ld3(FX, i) + h * v);
+    float q0 = s.at(FQ, i), q1 = s.at(FQ + 1, i), q2 = s.at(FQ + 2, i), q3 = s.at(FQ + 3, i);
+    // [0, w] (x) q, world-frame angular velocity
+    float d0 = -w.x * q1 - w.y * q2 - w.z * q3;
+    float d1 = w.x * q0 + w.y * q3 - w.z * q2;
+    float d2 = -w.x * q3 + w.y * q0 + w.z * q1;
+    float d3 = w.x * q2 - w.y * q1 + w.z * q0;
+    float hh = 0.5f * h;
+    q0 += hh * d0; q1 += hh * d1; q2 += hh * d2; q3 += hh * d3;
+    float il = rsqrtf(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
+    s.at(FQ, i) = q0 * il; s.at(FQ + 1, i) = q1 * il; s.at(FQ + 2, i) = q2 * il; s.at(FQ + 3, i) = q3 * il;
+  }
+  __syncwarp();
+
+  // (11) position correction (Eq. baumgarte), colour by colour
+  colour_passes<2>(s, Bc, S, ncol, lane, Pm);
+
+  st.cur = cur;
+  st.npairs = npairs;
+  st.ncolours = ncol;
+  out.res = res;
+  out.sweeps = sweeps;
+  out.npairs = npairs;
+  out.npoints = npoints;
+  out.ncol = ncol;
+  return out;
+}
+
+// ----------------------------------------------------------------- episode
+__device__ __forceinline__ float body_kinetic(const Sm& s, const Dev& D, int gi, int i) {
+  float m = D.mass[gi];
+  float3 v = s.ld3(FV, i), w = s.ld3(FW, i);
+  // body-frame angular velocity R^T w and I = 1 / invI
+  float wl0 = dot(s.axis(i, 0), w), wl1 = dot(s.axis(i, 1), w), wl2 = dot(s.axis(i, 2), w);
+  float I0 = 1.f / D.invI[gi], I1 = 1.f / D.invI[D.B + gi], I2 = 1.f / D.invI[2 * D.B + gi];
+  return 0.5f * m * dot(v, v) + 0.5f * (I0 * wl0 * wl0 + I1 * wl1 * wl1 + I2 * wl2 * wl2);
+}
+
+struct Terms { float ek, dxr, cmin; int nfallen; };
+
+// Eq. collapse terms over active dynamic blocks except `skip` (frames must be current).
+__device__ Terms collapse_terms(const Dev& D, const Ep& E, int skip) {
+  const Sm& s = E.s;
+  float ek = 0.f, dxr = 0.f, cmin = 1.f;
+  int nf = 0;
+  for (int i = E.lane; i < E.nb; i += 32) {
+    int fl = s.flags[i];
+    if (!(fl & kActive) || (fl & kStatic) || i == skip) continue;
+    int gi = E.b0 + i;
+    ek += body_kinetic(s, D, gi, i);
+    float3 d = s.ld3(FX, i) - f3(D.x0[gi], D.x0[D.B + gi], D.x0[2 * D.B + gi]);
+    float r = sqrtf(dot(d, d)) / (2.f * s.at(FH, i));
+    dxr = fmaxf(dxr, r);
+    nf += r > D.P.fall_frac;
+    float3 z = s.axis(i, 2);
+    float c = dot(z, f3(D.z0[gi], D.z0[D.B + gi], D.z0[2 * D.B + gi]));
+    cmin = fminf(cmin, c);
+  }
+  Terms t;
+  t.ek = warp_sum(ek);
+  t.dxr = warp_max(dxr);
+  t.cmin = warp_min(cmin);
+  t.nfallen = (int)warp_sum((float)nf);
+  return t;
+}
+
+__device__ void refresh_frames(const Dev& D, const Ep& E) {
+  for (int i = E.lane; i < E.nb; i += 32) body_frame(E.s, D, E.b0 + i, i);
+  __syncwarp();
+}
+
+// Starts move st.mi: a constant force F = sign * factor * k * mu_s * m * |g|
+// (Sec. 5) along the block's axis, fixed at the start of the push.
+__device__ void start_move(const Dev& D, const Ep& E, EpState& st) {
+  int m = D.mv_off[E.e] + st.mi;
+  int blk = D.mv_block[m];
+  if (E.lane == 0) {
+    int gi = E.b0 + blk;
+    const Sm& s = E.s;
+    float3 dir = s.axis(blk, D.mv_axis[m] == JB_AXIS_Y ? 0 : 1);
+    float g = sqrtf(D.P.g[0] * D.P.g[0] + D.P.g[1] * D.P.g[1] + D.P.g[2] * D.P.g[2]);
+    float F = D.mv_sign[m] * D.mv_factor[m] * D.mv_k[m] * D.mu[gi] * D.mass[gi] * g;
+    D.f[gi] = F * dir.x; D.f[D.B + gi] = F * dir.y; D.f[2 * D.B + gi] = F * dir.z;
+    D.f_steps[gi] = D.mv_push[m];
+  }
+  __syncwarp();
+  st.pb = blk;
+  st.phase = JB_PH_PUSH;
+  st.remaining = D.mv_push[m];
+}
+
+__device__ void end_push(const Dev& D, const Ep& E, const EpState& st) {
+  if (st.pb >= 0 && E.lane == 0) {
+    int gi = E.b0 + st.pb;
+    D.f[gi] = 0.f; D.f[D.B + gi] = 0.f; D.f[2 * D.B + gi] = 0.f;
+    D.f_steps[gi] = 0;
+  }
+  __syncwarp();
+}
+
+__device__ void next_move(const Dev& D, const Ep& E, EpState& st) {
+  st.mi++;
+  int nm = D.mv_off[E.e + 1] - D.mv_off[E.e];
+  if (st.mi < nm) start_move(D, E, st);
+  else st.phase = JB_PH_DONE;
+}
+
+__device__ void run_episode(const Dev& D, int e, int mode, int max_steps, unsigned char* base, int lane) {
+  Ep E;
+  E.e = e;
+  E.lane = lane;
+  E.b0 = D.body_off[e];
+  E.nb = D.body_off[e + 1] - E.b0;
+  E.Pc = pair_capacity(E.nb);
+  E.poff = D.pair_off[e];
+  E.s = sm_view(base, D.nb_max, D.pc_max, D.ps);
+  const Sm& s = E.s;
+  EpState st = D.ep[e];
+  if (mode == kModeFree && st.phase != JB_PH_FREE) return;
+  if (mode == kModeProtocol && (st.phase == JB_PH_FREE || st.phase == JB_PH_DONE)) return;
+
+  for (int i = lane; i < E.nb; i += 32) {
+    int gi = E.b0 + i;
+    for (int k = 0; k < 3; ++k) {
+      s.at(FX + k, i) = D.x[k * D.B + gi];
+      s.at(FV + k, i) = D.v[k * D.B + gi];
+      s.at(FW + k, i) = D.w[k * D.B + gi];
+      s.at(FH + k, i) = D.half[k * D.B + gi];
+    }
+    for (int k = 0; k < 4; ++k) s.at(FQ + k, i) = D.q[k * D.B + gi];
+    s.at(FM, i) = D.invm[gi];
+    s.at(FMU, i) = D.mu[gi];
+    s.flags[i] = D.flags[gi];
+  }
+  if (lane == 0) {   // ground slot
+    int G = E.nb;
+    for (int k = 0; k < 3; ++k) { s.at(FX + k, G) = 0.f; s.at(FV + k, G) = 0.f; s.at(FW + k, G) = 0.f; s.at(FH + k, G) = 0.f; }
+    s.at(FQ, G) = 1.f; s.at(FQ + 1, G) = 0.f; s.at(FQ + 2, G) = 0.f; s.at(FQ + 3, G) = 0.f;
+    s.at(FM, G) = 0.f;
+    s.at(FMU, G) = D.ground_mu[e];
+    s.flags[G] = kActive | kStatic;
+  }
+  __syncwarp();
+  if (lane == 0) body_frame(s, D, -1, E.nb);
+  __syncwarp();
+
+  const float h = D.P.dt / (float)D.P.n_sub;
+  for (int step = 0; step < max_steps; ++step) {
+    if (mode == kModeProtocol && st.phase == JB_PH_DONE) break;
+    int ndyn = 0, nact = 0;
+    for (int i = lane; i < E.nb; i += 32) {
+      ndyn += (s.flags[i] & kActive) && !(s.flags[i] & kStatic);
+      nact += (s.flags[i] & kActive) != 0;
+    }
+    ndyn = __reduce_add_sync(FULL, ndyn);
+    nact = __reduce_add_sync(FULL, nact);
+    st.body_steps += ndyn;
+    StepOut o;
+    for (int sub = 0; sub < D.P.n_sub; ++sub) {
+      o = substep(D, E, st, h);
+      st.status |= o.status;
+      st.last_sweeps = o.sweeps;
+      st.last_res = o.res;
+      if (!(o.res <= st.max_res)) st.max_res = o.res;
+      st.total_sweeps += o.sweeps;
+      st.solves += 1.0;
+      st.npoints = o.npoints;
+      st.max_colours = max(st.max_colours, o.ncol);
+      st.point_sweeps += (double)o.npoints * o.sweeps;
+      st.point_steps += o.npoints;
+      st.pair_steps += o.npairs;
+      st.bp_tests += 0.5 * nact * (nact - 1) + ndyn;
+    }
+    for (int i = lane; i < E.nb; i += 32) {
+      int gi = E.b0 + i;
+      if (D.f_steps[gi] > 0) D.f_steps[gi] -= 1;
+    }
+    st.steps++;
+    bool bad = false;
+    for (int i = lane; i < E.nb; i += 32) {
+      float t = s.at(FX, i) + s.at(FX + 1, i) + s.at(FX + 2, i) + s.at(FV, i) + s.at(FV + 1, i) + s.at(FV + 2, i) +
+                s.at(FW, i) + s.at(FW + 1, i) + s.at(FW + 2, i);
+      if (!isfinite(t)) bad = true;
+    }
+    __syncwarp();
+    if (__any_sync(FULL, bad)) {
+      st.status |= JB_EP_NONFINITE;
+      if (st.phase != JB_PH_FREE) st.phase = JB_PH_DONE;
+      break;
+    }
+    if (mode != kModeProtocol) continue;
+
+    refresh_frames(D, E);
+    int skip = st.phase == JB_PH_PUSH ? st.pb : -1;
+    Terms t = collapse_terms(D, E, skip);
+    bool coll = t.dxr > D.P.fall_frac && t.ek > D.P.collapse_ek && t.cmin < D.P.collapse_cos;
+    if ((st.phase == JB_PH_PUSH || st.phase == JB_PH_SETTLE) && coll) {
+      st.collapsed = 1;
+      if (st.phase == JB_PH_PUSH) end_push(D, E, st);
+      st.pb = -1;
+      st.phase = JB_PH_REST;
+      st.rest_left = D.P.rest_steps;
+      continue;
+    }
+    if (st.phase == JB_PH_PUSH) {
+      if (--st.remaining <= 0) {
+        end_push(D, E, st);
+        int m = D.mv_off[e] + st.mi;
+        if (D.mv_remove[m]) {
+          if (lane == 0) s.flags[st.pb] &= ~kActive;
+          __syncwarp();
+        }
+        st.pb = -1;
+        st.phase = JB_PH_SETTLE;
+        st.remaining = D.mv_settle[m];
+        if (st.remaining <= 0) next_move(D, E, st);
+      }
+    } else if (st.phase == JB_PH_SETTLE) {
+      if (--st.remaining <= 0) next_move(D, E, st);
+    } else if (st.phase == JB_PH_REST) {
+      Terms ta = collapse_terms(D, E, -1);
+      st.rest_left--;
+      if (ta.ek < D.P.rest_ek) { st.resting = 1; st.phase = JB_PH_DONE; }
+      else if (st.rest_left <= 0) st.phase = JB_PH_DONE;
+    }
+  }
+
+  for (int i = lane; i < E.nb; i += 32) {
+    int gi = E.b0 + i;
+    for (int k = 0; k < 3; ++k) {
+      D.x[k * D.B + gi] = s.at(FX + k, i);
+      D.v[k * D.B + gi] = s.at(FV + k, i);
+      D.w[k * D.B + gi] = s.at(FW + k, i);
+    }
+    for (int k = 0; k < 4; ++k) D.q[k * D.B + gi] = s.at(FQ + k, i);
+    D.flags[gi] = s.flags[i];
+  }
+  if (lane == 0) D.ep[e] = st;
+  __syncwarp();
+}
+
+// Persistent grid: each warp claims episodes from the work counter.
+__global__ void __launch_bounds__(kWarpsPerCta * 32) episode_kernel(Dev D, int mode, int max_steps) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char* base = smem + (size_t)warp * D.smem_per_warp;
+  for (;;) {
+    int idx = 0;
+    if (lane == 0) idx = atomicAdd(D.work_counter, 1);
+    idx = __shfl_sync(FULL, idx, 0);
+    if (idx >= D.E) break;
+    int e = D.order ? D.order[idx] : idx;
+    run_episode(D, e, mode, max_steps, base, lane);
+  }
+}
+
+// ------------------------------------------------------------ init / commands
+// Derived per-body state: normalised q, inverse mass, body inverse inertia
+// (Eq. inertia), collapse reference pose; episode state reset.
+__global__ void init_bodies_kernel(Dev D) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= D.B) return;
+  float q0 = D.q[b], q1 = D.q[D.B + b], q2 = D.q[2 * D.B + b], q3 = D.q[3 * D.B + b];
+  float il = rsqrtf(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
+  q0 *= il; q1 *= il; q2 *= il; q3 *= il;
+  D.q[b] = q0; D.q[D.B + b] = q1; D.q[2 * D.B + b] = q2; D.q[3 * D.B + b] = q3;
+  float m = D.mass[b];
+  bool st = !(m > 0.f);
+  float l = 2.f * D.half[b], wd = 2.f * D.half[D.B + b], th = 2.f * D.half[2 * D.B + b];
+  if (st) {
+    D.invm[b] = 0.f;
+    for (int k = 0; k < 3; ++k) { D.invI[k * D.B + b] = 0.f; D.v[k * D.B + b] = 0.f; D.w[k * D.B + b] = 0.f; }
+  } else {
+    D.invm[b] = 1.f / m;
+    D.invI[b] = 12.f / (m * (wd * wd + th * th));
+    D.invI[D.B + b] = 12.f / (m * (l * l + th * th));
+    D.invI[2 * D.B + b] = 12.f / (m * (l * l + wd * wd));
+  }
+  D.flags[b] = kActive | (st ? kStatic : 0);
+  for (int k = 0; k < 3; ++k) { D.x0[k * D.B + b] = D.x[k * D.B + b]; D.f[k * D.B + b] = 0.f; }
+  D.f_steps[b] = 0;
+  // thickness axis = third column of R(q)
+  D.z0[b] = 2.f * (q1 * q3 + q2 * q0);
+  D.z0[D.B + b] = 2.f * (q2 * q3 - q1 * q0);
+  D.z0[2 * D.B + b] = 1.f - 2.f * (q1 * q1 + q2 * q2);
+}
+
+__global__ void init_episodes_kernel(Dev D) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= D.E) return;
+  EpState s;
+  memset(&s, 0, sizeof s);
+  s.phase = JB_PH_FREE;
+  s.pb = -1;
+  D.ep[e] = s;
+}
+
+// Resets the collapse reference to the current poses.
+__global__ void reset_reference_kernel(Dev D) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= D.B) return;
+  float q0 = D.q[b], q1 = D.q[D.B + b], q2 = D.q[2 * D.B + b], q3 = D.q[3 * D.B + b];
+  float il = rsqrtf(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
+  q0 *= il; q1 *= il; q2 *= il; q3 *= il;
+  D.q[b] = q0; D.q[D.B + b] = q1; D.q[2 * D.B + b] = q2; D.q[3 * D.B + b] = q3;
+  for (int k = 0; k < 3; ++k) D.x0[k * D.B + b] = D.x[k * D.B + b];
+  D.z0[b] = 2.f * (q1 * q3 + q2 * q0);
+  D.z0[D.B + b] = 2.f * (q2 * q3 - q1 * q0);
+  D.z0[2 * D.B + b] = 1.f - 2.f * (q1 * q1 + q2 * q2);
+}
+
+__global__ void clear_cache_kernel(Dev D) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= D.E) return;
+  D.ep[e].npairs = 0;
+  D.ep[e].ncolours = 0;
+}
+
+__device__ __forceinline__ float3 body_axis_g(const Dev& D, int gi, int k) {
+  float w = D.q[gi], x = D.q[D.B + gi], y = D.q[2 * D.B + gi], z = D.q[3 * D.B + gi];
+  if (k == 0) return f3(1 - 2 * (y * y + z * z), 2 * (x * y + z * w), 2 * (x * z - y * w));
+  if (k == 1) return f3(2 * (x * y - z * w), 1 - 2 * (x * x + z * z), 2 * (y * z + x * w));
+  return f3(2 * (x * z + y * w), 2 * (y * z - x * w), 1 - 2 * (x * x + y * y));
+}
+
+// Starts every episode's schedule (move 0) or marks it done.
+__global__ void protocol_start_kernel(Dev D) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= D.E) return;
+  EpState s = D.ep[e];
+  s.mi = 0;
+  s.pb = -1;
+  s.collapsed = 0;
+  s.resting = 0;
+  int m0 = D.mv_off[e], nm = D.mv_off[e + 1] - m0;
+  if (nm <= 0) { s.phase = JB_PH_DONE; D.ep[e] = s; return; }
+  int blk = D.mv_block[m0];
+  int gi = D.body_off[e] + blk;
+  float3 dir = body_axis_g(D, gi, D.mv_axis[m0] == JB_AXIS_Y ? 0 : 1);
+  float g = sqrtf(D.P.g[0] * D.P.g[0] + D.P.g[1] * D.P.g[1] + D.P.g[2] * D.P.g[2]);
+  float F = D.mv_sign[m0] * D.mv_factor[m0] * D.mv_k[m0] * D.mu[gi] * D.mass[gi] * g;
+  D.f[gi] = F * dir.x; D.f[D.B + gi] = F * dir.y; D.f[2 * D.B + gi] = F * dir.z;
+  D.f_steps[gi] = D.mv_push[m0];
+  s.pb = blk;
+  s.phase = JB_PH_PUSH;
+  s.remaining = D.mv_push[m0];
+  D.ep[e] = s;
+}
+
+__global__ void push_kernel(Dev D, int n, const int* ep, const int* blk, const int* axis, const float* force, const int* steps) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int gi = D.body_off[ep[i]] + blk[i];
+  float3 dir = body_axis_g(D, gi, axis[i] == JB_AXIS_Y ? 0 : 1);
+  D.f[gi] = force[i] * dir.x; D.f[D.B + gi] = force[i] * dir.y; D.f[2 * D.B + gi] = force[i] * dir.z;
+  D.f_steps[gi] = steps[i];
+}
+
+__global__ void remove_kernel(Dev D, int n, const int* ep, const int* blk) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int gi = D.body_off[ep[i]] + blk[i];
+  D.flags[gi] &= ~kActive;
+  D.f_steps[gi] = 0;
+}
+
+// Eq. stability margin and Sec. 8 statistics, one thread per episode.  The
+// support polygon is the convex hull (gift wrapping) of the xy corners of the
+// ground-touching blocks; imbalance = minus the smallest signed distance from
+// the COM to the hull edges (distance to the segment/point if degenerate).
+__device__ __forceinline__ float2 corner_xy(const Dev& D, int gi, int c) {
+  float3 a0 = body_axis_g(D, gi, 0), a1 = body_axis_g(D, gi, 1), a2 = body_axis_g(D, gi, 2);
+  float s0 = (c & 1) ? 1.f : -1.f, s1 = (c & 2) ? 1.f : -1.f, s2 = (c & 4) ? 1.f : -1.f;
+  float hx = D.half[gi], hy = D.half[D.B + gi], hz = D.half[2 * D.B + gi];
+  return make_float2(D.x[gi] + s0 * hx * a0.x + s1 * hy * a1.x + s2 * hz * a2.x,
+                     D.x[D.B + gi] + s0 * hx * a0.y + s1 * hy * a1.y + s2 * hz * a2.y);
+}
+
+__device__ __forceinline__ bool touching(const Dev& D, int gi) {
+  if (!(D.flags[gi] & kActive) || (D.flags[gi] & kStatic)) return false;
+  float3 a0 = body_axis_g(D, gi, 0), a1 = body_axis_g(D, gi, 1), a2 = body_axis_g(D, gi, 2);
+  float ez = fabsf(a0.z) * D.half[gi] + fabsf(a1.z) * D.half[D.B + gi] + fabsf(a2.z) * D.half[2 * D.B + gi];
+  return D.x[2 * D.B + gi] - ez <= D.P.aabb_eps;
+}
+
+__global__ void stats_kernel(Dev D, jb_episode_stats* out) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= D.E) return;
+  int b0 = D.body_off[e], nb = D.body_off[e + 1] - b0;
+  EpState st = D.ep[e];
+  double cx = 0, cy = 0, mt = 0;
+  float ek = 0.f;
+  int nf = 0;
+  for (int i = 0; i < nb; ++i) {
+    int gi = b0 + i;
+    if (!(D.flags[gi] & kActive) || (D.flags[gi] & kStatic)) continue;
+    float m = D.mass[gi];
+    cx += m * D.x[gi]; cy += m * D.x[D.B + gi]; mt += m;
+    float3 v = f3(D.v[gi], D.v[D.B + gi], D.v[2 * D.B + gi]);
+    float3 w = f3(D.w[gi], D.w[D.B + gi], D.w[2 * D.B + gi]);
+    float wl0 = dot(body_axis_g(D, gi, 0), w), wl1 = dot(body_axis_g(D, gi, 1), w), wl2 = dot(body_axis_g(D, gi, 2), w);
+    ek += 0.5f * m * dot(v, v) + 0.5f * (wl0 * wl0 / D.invI[gi] + wl1 * wl1 / D.invI[D.B + gi] + wl2 * wl2 / D.invI[2 * D.B + gi]);
+    float3 d = f3(D.x[gi] - D.x0[gi], D.x[D.B + gi] - D.x0[D.B + gi], D.x[2 * D.B + gi] - D.x0[2 * D.B + gi]);
+    if (sqrtf(dot(d, d)) / (2.f * D.half[gi]) > D.P.fall_frac) ++nf;
+  }
+  float imb = 0.f;
+  if (mt > 0) {
+    float comx = (float)(cx / mt), comy = (float)(cy / mt);
+    // lowest (x, y) corner as the start of the wrap
+    float2 p0 = make_float2(FLT_MAX, FLT_MAX);
+    int ncorner = 0;
+    for (int i = 0; i < nb; ++i) {
+      int gi = b0 + i;
+      if (!touching(D, gi)) continue;
+      for (int c = 0; c < 8; ++c) {
+        float2 p = corner_xy(D, gi, c);
+        ++ncorner;
+        if (p.x < p0.x || (p.x == p0.x && p.y < p0.y)) p0 = p;
+      }
+    }
+    if (ncorner > 0) {
+      float dmin = FLT_MAX;
+      float2 cur = p0;
+      int nh = 0;
+      float2 first_next = p0;
+      bool degenerate = true;
+      // gift wrapping: next = the point with every other point to its left
+      for (int it = 0; it < 8 * nb + 2; ++it) {
+        float2 nxt = cur;
+        bool have = false;
+        for (int i = 0; i < nb; ++i) {
+          int gi = b0 + i;
+          if (!touching(D, gi)) continue;
+          for (int c = 0; c < 8; ++c) {
+            float2 p = corner_xy(D, gi, c);
+            if (p.x == cur.x && p.y == cur.y) continue;
+            if (!have) { nxt = p; have = true; continue; }
+            float cr = (nxt.x - cur.x) * (p.y - cur.y) - (nxt.y - cur.y) * (p.x - cur.x);
+            float dn = (nxt.x - cur.x) * (nxt.x - cur.x) + (nxt.y - cur.y) * (nxt.y - cur.y);
+            float dp = (p.x - cur.x) * (p.x - cur.x) + (p.y - cur.y) * (p.y - cur.y);
+            if (cr < 0.f || (cr == 0.f && dp > dn)) nxt = p;
+          }
+        }
+        if (!have) break;
+        if (nh == 0) first_next = nxt;
+        float ex = nxt.x - cur.x, ey = nxt.y - cur.y;
+        float len = sqrtf(ex * ex + ey * ey);
+        if (len > 0.f) {
+          float sd = (ex * (comy - cur.y) - ey * (comx - cur.x)) / len;
+          dmin = fminf(dmin, sd);
+        }
+        ++nh;
+        cur = nxt;
+        if (cur.x == p0.x && cur.y == p0.y) break;
+      }
+      degenerate = nh < 3;
+      if (!degenerate) imb = -dmin;
+      else if (nh == 0) {
+        float dx = comx - p0.x, dy = comy - p0.y;
+        imb = sqrtf(dx * dx + dy * dy);
+      } else {
+        float2 a = p0, b = first_next;
+        float ex = b.x - a.x, ey = b.y - a.y;
+        float l2 = ex * ex + ey * ey;
+        float t = l2 > 0.f ? fminf(fmaxf(((comx - a.x) * ex + (comy - a.y) * ey) / l2, 0.f), 1.f) : 0.f;
+        float dx = comx - (a.x + t * ex), dy = comy - (a.y + t * ey);
+        imb = sqrtf(dx * dx + dy * dy);
+      }
+    }
+  }
+  jb_episode_stats o;
+  o.status = st.status;
+  o.phase = st.phase;
+  o.collapsed = st.collapsed;
+  o.resting = st.resting || ek < D.P.rest_ek;
+  o.n_fallen = nf;
+  o.moves_done = st.mi;
+  o.n_pairs = st.npairs;
+  o.n_points = st.npoints;
+  o.last_sweeps = st.last_sweeps;
+  o.steps = st.steps;
+  o.max_colours = st.max_colours;
+  o.reserved = 0;
+  o.com_imbalance = imb;
+  o.kinetic = ek;
+  o.last_residual = st.last_res;
+  o.max_residual = st.max_res;
+  o.total_sweeps = st.total_sweeps;
+  o.solves = st.solves;
+  o.body_steps = st.body_steps;
+  o.point_sweeps = st.point_sweeps;
+  o.point_steps = st.point_steps;
+  o.pair_steps = st.pair_steps;
+  o.bp_tests = st.bp_tests;
+  out[e] = o;
+}
+
+}  // namespace jbk

@@ -102,7 +102,9 @@ class Protocol:
 
 def tower_bodies(t: Tower, seed: int, episode: int):
     """Initial poses and masses of one tower (float32)."""
-    L, W, H = t.dims
+    # tower parameters are single precision, as in the C tower descriptor
+    L, W, H = (float(np.float32(d)) for d in t.dims)
+    m0, jit = float(np.float32(t.mass)), float(np.float32(t.mass_jitter))
     n = t.levels * t.per_level
     half = np.empty((3, n), np.float32)
     x = np.zeros((3, n), np.float32)
@@ -121,7 +123,7 @@ def tower_bodies(t: Tower, seed: int, episode: int):
                 x[:, i] = (off, 0.0, z)
                 q[:, i] = (c, 0.0, 0.0, c)     # +90 degrees about z
     u = u01(seed, episode, S_MASS, np.arange(n))
-    mass = (t.mass * (1.0 + t.mass_jitter * (2.0 * u - 1.0))).astype(np.float32)
+    mass = (m0 * (1.0 + jit * (2.0 * u - 1.0))).astype(np.float32)
     return half, x, q, mass
 
 
@@ -279,3 +281,38 @@ def subset(scene: Scene, prot: Protocol, episodes):
     p = Protocol(moff, *[getattr(prot, f)[midx] for f in
                          ("block", "axis", "sign", "factor", "k", "remove", "push_steps", "settle_steps")])
     return s, p
+
+
+def pile_scene(n_boxes=24, seed=0, spread=0.09, height=0.06, dims=(0.075, 0.025, 0.015),
+               mass=0.015, mu=0.4):
+    """One episode of randomly oriented blocks scattered over a small region
+    (many touching or slightly interpenetrating pairs, all contact kinds)."""
+    idx = np.arange(n_boxes)
+    ux, uy, uz = (u01(seed, 0, S_LEVEL + k, idx) for k in range(3))
+    qv = np.stack([u01(seed, 0, S_SLOT + k, idx) * 2.0 - 1.0 for k in range(4)])
+    qv /= np.linalg.norm(qv, axis=0, keepdims=True)
+    boxes = []
+    for i in range(n_boxes):
+        boxes.append(dict(half=tuple(d / 2 for d in dims),
+                          x=((ux[i] - 0.5) * spread, (uy[i] - 0.5) * spread, 0.012 + uz[i] * height),
+                          q=tuple(qv[:, i]), mass=mass, mu=mu))
+    return custom_scene(boxes, ground_mu=mu)
+
+
+def perturbed(scene: Scene, seed: int, dx=3e-4, dang=0.01) -> Scene:
+    """Copy of a scene with every pose jittered (translation +-dx, small rotation
+    of about dang radians)."""
+    B = scene.n_bodies
+    idx = np.arange(B)
+    d = np.stack([u01(seed, 1, S_LEVEL + k, idx) * 2 - 1 for k in range(3)]) * dx
+    r = np.stack([u01(seed, 1, S_SLOT + k, idx) * 2 - 1 for k in range(3)]) * (dang / 2)
+    q = scene.q.astype(np.float64)
+    dq = np.vstack([np.ones(B), r])
+    w1, x1, y1, z1 = dq
+    w2, x2, y2, z2 = q
+    nq = np.stack([w1 * w2 - x1 * x2 - y1 * y2 - z1 * z2, w1 * x2 + x1 * w2 + y1 * z2 - z1 * y2,
+                   w1 * y2 - x1 * z2 + y1 * w2 + z1 * x2, w1 * z2 + x1 * y2 - y1 * x2 + z1 * w2])
+    nq /= np.linalg.norm(nq, axis=0, keepdims=True)
+    return Scene(scene.body_off.copy(), scene.half.copy(), scene.mass.copy(), scene.mu.copy(),
+                 (scene.x + d).astype(np.float32), nq.astype(np.float32), scene.v.copy(),
+                 scene.w.copy(), scene.ground_mu.copy())

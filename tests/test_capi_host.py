@@ -1,0 +1,76 @@
+"""C-ABI library checks that need no GPU: it loads, exports every entry point
+declared in include/jb.h, and its host-only helpers behave."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "jb.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(jb_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("jb_batch_create", "jb_step", "jb_run_protocol", "jb_apply_push", "jb_remove_block",
+                 "jb_read_state", "jb_read_contacts", "jb_read_episode_stats", "jb_sync",
+                 "jb_save_state", "jb_load_state", "jb_batch_destroy", "jb_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    import paper_2606_28394_gb300 as jb
+    lib = C.CDLL(jb.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(declared_functions()) <= set(jb.EXPORTS)
+
+
+def test_default_params_follow_the_paper_table():
+    import paper_2606_28394_gb300 as jb
+    p = jb.default_params()
+    assert abs(p.dt - 1 / 240) < 1e-9 and abs(p.restitution - 0.10) < 1e-7
+    assert abs(p.beta - 0.35) < 1e-7 and abs(p.slop - 4e-4) < 1e-10 and abs(p.aabb_eps - 2e-3) < 1e-10
+    assert abs(p.gravity[2] + 9.81) < 1e-6
+
+
+def test_tower_builder_matches_generator_bit_exactly():
+    import paper_2606_28394_gb300 as jb
+    towers = [synth.Tower(levels=18, mu=0.4), synth.Tower(levels=7, mu=0.25), synth.Tower(levels=30, mu=0.6)]
+    seed = 12345
+    ref = synth.build_scene(towers, seed)
+    E = len(towers)
+    desc = (jb.jb_tower_desc * E)()
+    for i, t in enumerate(towers):
+        desc[i].levels = t.levels; desc[i].per_level = t.per_level
+        desc[i].dims = (C.c_float * 3)(*t.dims); desc[i].mass = t.mass
+        desc[i].mass_jitter = t.mass_jitter; desc[i].mu_s = t.mu
+    off = np.zeros(E + 1, np.int32)
+    assert jb.jb_tower_layout(desc, E, off.ctypes.data_as(jb._ip)) == 0
+    assert (off == ref.body_off).all()
+    B = int(off[-1])
+    half = np.zeros((3, B), np.float32); mass = np.zeros(B, np.float32); mu = np.zeros(B, np.float32)
+    x = np.zeros((3, B), np.float32); q = np.zeros((4, B), np.float32); gmu = np.zeros(E, np.float32)
+    f = lambda a: a.ctypes.data_as(jb._fp)
+    assert jb.jb_tower_init(desc, E, seed, off.ctypes.data_as(jb._ip), f(half), f(mass), f(mu), f(x), f(q), f(gmu)) == 0
+    assert (half == ref.half).all() and (mass == ref.mass).all() and (mu == ref.mu).all()
+    assert (x == ref.x).all() and (q == ref.q).all() and (gmu == ref.ground_mu).all()
+
+
+def test_host_argument_errors_need_no_device():
+    import paper_2606_28394_gb300 as jb
+    p = jb.default_params()
+    off = np.array([0, 3], np.int32)
+    assert jb.jb_workspace_bytes(0, off.ctypes.data_as(jb._ip), C.byref(p), 0) == 0
+    assert jb.jb_workspace_bytes(1, off.ctypes.data_as(jb._ip), C.byref(p), 0) > 0
+    assert jb.jb_tower_layout(None, 1, off.ctypes.data_as(jb._ip)) == jb.JB_EINVAL
+    assert b"null" in jb.jb_last_error()
+    h = C.c_void_p()
+    assert jb.jb_batch_create(None, C.byref(p), 0, None, 0, None, C.byref(h)) == jb.JB_EINVAL

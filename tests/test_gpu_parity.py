@@ -1,0 +1,246 @@
+"""GPU (FP32, coloured PGS) against the FP64 oracle, through the C ABI.
+
+Tolerances:
+  - contact sets: identical pairs (a, b, SAT axis, reference/incident features)
+    except pairs whose separation is within 1e-6 m of the -margin threshold;
+    depths and point offsets along the normal within 2e-6 m (FP32 rounding of
+    0.3 m coordinates is ~3e-8 m per operation), offsets in the contact plane
+    within 2e-5 m (a clip vertex where an incident edge meets a side plane at
+    a shallow angle theta is only determined to ~eps32 |x| / sin(theta)),
+    normals within 1e-5;
+  - one step from an identical state with both solvers converged to a PGS
+    residual <= 1e-5 m/s: positions within 1e-5 m, velocities within 1e-4 m/s
+    (angular velocity scaled by the block's half diagonal).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+MC = 1e-3   # contact margin
+
+
+def jb():
+    import paper_2606_28394_gb300 as m
+    return m
+
+
+def as64(scene):
+    s = synth.Scene(scene.body_off, *[getattr(scene, k).astype(np.float64) for k in
+                                      ("half", "mass", "mu", "x", "q", "v", "w", "ground_mu")])
+    return s
+
+
+def gpu_contacts(batch, e):
+    arr = jb().contacts_as_arrays(batch.contacts(e))
+    pairs = {}
+    for i in range(len(arr["a"])):
+        key = (int(arr["a"][i]), int(arr["b"][i]))
+        d = pairs.setdefault(key, dict(axis=int(arr["axis"][i]), ref=int(arr["ref_face"][i]),
+                                       inc=int(arr["inc_face"][i]), n=arr["n"][i], p=[], depth=[], lam=[]))
+        d["p"].append(arr["p"][i]); d["depth"].append(arr["depth"][i]); d["lam"].append(arr["lam"][i])
+    return pairs
+
+
+def oracle_contacts(world, e):
+    out = {}
+    for r in oracle.contact_dicts(world.contacts(e)):
+        out[(r["a"], r["b"])] = dict(axis=r["axis"], ref=r["ref_face"], inc=r["inc_face"], n=r["n"],
+                                     p=list(r["p"]), depth=list(r["depth"]), lam=list(r["lam"]))
+    return out
+
+
+def near_threshold(scene, e, key, tol=1e-6):
+    """True if the pair's detection sits within tol of the margin threshold (FP64)."""
+    a, b = key
+    o = scene.body_off[e]
+    S = as64(scene)
+    xb, qb, hb = S.x[:, o + b], S.q[:, o + b], S.half[:, o + b]
+    if a < 0:
+        R = oracle.rotmat(qb / np.linalg.norm(qb))
+        zs = [xb[2] + R[2] @ (np.array([sx, sy, sz]) * hb) for sx in (-1, 1) for sy in (-1, 1) for sz in (-1, 1)]
+        return min(abs(z - MC) for z in zs) < tol
+    r = oracle.sat(S.x[:, o + a], S.q[:, o + a], S.half[:, o + a], xb, qb, hb, margin=MC)
+    return abs(r["dmin"] + MC) < tol
+
+
+def compare_contact_sets(scene, g, o, e=0):
+    only_g = set(g) - set(o)
+    only_o = set(o) - set(g)
+    for key in only_g | only_o:
+        assert near_threshold(scene, e, key), ("pair only on one side", key, key in g)
+    n_pts = 0
+    for key in set(g) & set(o):
+        G, O = g[key], o[key]
+        assert (G["axis"], G["ref"], G["inc"]) == (O["axis"], O["ref"], O["inc"]), key
+        assert np.abs(np.asarray(G["n"]) - O["n"]).max() < 1e-5, key
+        pg, po = np.asarray(G["p"]), np.asarray(O["p"])
+        dg, do = np.asarray(G["depth"]), np.asarray(O["depth"])
+        if len(pg) != len(po):
+            # only allowed when a point sits at the depth threshold
+            assert np.min(np.abs(np.r_[dg, do] + MC)) < 1e-6, key
+            continue
+        nrm = np.asarray(O["n"])
+        for i in range(len(pg)):
+            j = np.argmin(np.linalg.norm(po - pg[i], axis=1))
+            d = po[j] - pg[i]
+            # across the face: FP32 rounding of the geometry; along the face: a
+            # clip vertex on an edge meeting a side plane at a shallow angle
+            # theta moves by ~eps32 |x| / sin(theta)
+            assert abs(d @ nrm) < 2e-6 and abs(do[j] - dg[i]) < 2e-6, (key, pg[i], po[j])
+            assert np.linalg.norm(d - (d @ nrm) * nrm) < 2e-5, (key, pg[i], po[j])
+        n_pts += len(pg)
+    return n_pts
+
+
+def step_both(scene, prm, n=1):
+    b = jb().Batch(scene, prm)
+    w = oracle.World(as64(scene), prm)
+    b.step(n)
+    w.step(n)
+    return b, w
+
+
+SCENES = {
+    "tower18": lambda: synth.build_scene([synth.Tower()], 0),
+    "tower18_perturbed": lambda: synth.perturbed(synth.build_scene([synth.Tower()], 0), 3, dx=3e-4, dang=0.02),
+    "pile": lambda: synth.pile_scene(28, seed=5),
+    "pile2": lambda: synth.pile_scene(40, seed=11, spread=0.12),
+}
+
+
+@pytest.mark.parametrize("name", sorted(SCENES))
+def test_contact_sets_match_oracle(cuda_device, name):
+    scene = SCENES[name]()
+    prm = synth.params(pgs_iters=1)
+    b, w = step_both(scene, prm)
+    g, o = gpu_contacts(b, 0), oracle_contacts(w, 0)
+    assert len(o) > 0
+    n = compare_contact_sets(scene, g, o)
+    assert n > 0
+
+
+def test_free_fall_closed_form_fp32(cuda_device):
+    sc = synth.custom_scene([dict(half=(0.0375, 0.0125, 0.0075), x=(0, 0, 2.0), mass=0.015)])
+    b = jb().Batch(sc, synth.params())
+    n = 37
+    b.step(n)
+    x, _, v, _ = b.state()
+    h = 1 / 240
+    assert abs(v[2, 0] + 9.81 * n * h) < 2e-6
+    assert abs(x[2, 0] - (2.0 - 9.81 * h * h * n * (n + 1) / 2)) < 2e-6
+
+
+def velocity_error(scene, v1, w1, v2, w2):
+    diag = np.sqrt((scene.half.astype(float) ** 2).sum(0))
+    return np.max(np.abs(v1 - v2)), np.max(np.abs(w1 - w2).max(0) * diag)
+
+
+@pytest.mark.parametrize("name,tol", [("tower4_perturbed", 1e-5), ("pile", 1e-5), ("tower18", 1e-5)])
+def test_one_step_converged_parity(cuda_device, name, tol):
+    if name == "tower4_perturbed":
+        scene = synth.perturbed(synth.build_scene([synth.Tower(levels=4, mu=0.5)], 1), 5, dx=2e-4, dang=0.01)
+    elif name == "pile":
+        scene = synth.pile_scene(28, seed=5)
+    else:
+        scene = synth.build_scene([synth.Tower()], 0)
+    prm = synth.params(residual_tol=tol, pgs_iter_cap=100000)
+    b, w = step_both(scene, prm)
+    st = b.stats()
+    assert st["status"][0] == 0 and st["last_residual"][0] <= tol
+    so = w.stats()
+    assert so["last_residual"][0] <= tol
+    xg, qg, vg, wg = b.state()
+    xo, qo, vo, wo = w.state()
+    assert np.abs(xg - xo).max() < 1e-5
+    ev, ew = velocity_error(scene, vg, wg, vo, wo)
+    assert ev < 1e-4 and ew < 1e-4, (ev, ew)
+
+
+def test_resting_tower_18_levels_gpu(cuda_device):
+    """The GPU path on the 18-level resting tower for 2 s: max penetration
+    < 1e-5 m and max point speed < 1e-4 m/s (as the oracle's pin)."""
+    scene = synth.build_scene([synth.Tower()], 0)
+    b = jb().Batch(scene, synth.params(residual_tol=1e-6, pgs_iter_cap=50000))
+    diag = np.sqrt((scene.half.astype(float) ** 2).sum(0))
+    maxpen = maxspeed = 0.0
+    for _ in range(48):
+        b.step(10)
+        _, _, v, w = b.state()
+        arr = jb().contacts_as_arrays(b.contacts(0))
+        maxpen = max(maxpen, arr["depth"].max())
+        maxspeed = max(maxspeed, (np.linalg.norm(v, axis=0) + np.linalg.norm(w, axis=0) * diag).max())
+    assert maxpen < 1e-5 and maxspeed < 1e-4, (maxpen, maxspeed)
+
+
+def test_push_force_threshold_gpu(cuda_device):
+    m = 0.0196
+    sc = synth.custom_scene([dict(half=(0.0405, 0.013, 0.009), x=(0, 0, 3.0), mass=m, mu=0.4)])
+    b = jb().Batch(sc, synth.params(), max_moves=1)
+    b.set_protocol(synth._protocol([[(0, synth.AXIS_Y, 1.0, 1.0, 3.0, 0, 1, 0)]], 1))
+    b.run_protocol(1)
+    _, _, v, _ = b.state()
+    F = m * v[0, 0] * 240
+    assert abs(F * 1e3 - 230.7) < 0.06
+
+
+def test_determinism_and_snapshot_resume(cuda_device):
+    scene = synth.perturbed(synth.build_scene([synth.Tower(levels=6), synth.Tower(levels=5)], 2), 4)
+    prm = synth.params(residual_tol=1e-5, pgs_iter_cap=20000)
+    a = jb().Batch(scene, prm)
+    a.step(10)
+    snap = a.save_state()
+    a.step(15)
+    xa = a.state()
+    b = jb().Batch(scene, prm)
+    b.step(25)
+    xb = b.state()
+    for u, v in zip(xa, xb):
+        assert np.array_equal(u, v)
+    a.load_state(snap)
+    a.step(15)
+    for u, v in zip(a.state(), xb):
+        assert np.array_equal(u, v)
+
+
+def test_protocol_runs_and_matches_oracle_outcomes(cuda_device):
+    """Removal rounds on short towers: both run the same schedule to the end;
+    towers that stand agree on the outcome (no collapse, nothing fallen)."""
+    towers = [synth.Tower(levels=5, mu=m) for m in (0.25, 0.4, 0.6, 0.4)]
+    scene = synth.build_scene(towers, 9)
+    prot = synth.removal_protocol(towers, 9, push_steps=30, settle_steps=60, max_removals=2)
+    prm = synth.params(residual_tol=1e-5, pgs_iter_cap=20000)
+    b = jb().Batch(scene, prm, max_moves=int(prot.off[-1]))
+    b.set_protocol(prot)
+    b.run_protocol()
+    w = oracle.World(as64(scene), prm)
+    w.set_protocol(prot)
+    w.run_protocol()
+    sg, so = b.stats(), w.stats()
+    assert (sg["phase"] == jb().JB_PH_DONE).all()
+    assert (so["phase"] == oracle.PH_DONE).all()
+    assert (sg["moves_done"] == so["moves_done"]).all()
+    agree = (sg["collapsed"] == so["collapsed"]).mean()
+    assert agree >= 0.75, (sg["collapsed"], so["collapsed"])
+    assert np.allclose(sg["body_steps"], so["body_steps"], rtol=0.25)
+
+
+def test_host_commands_and_removal(cuda_device):
+    scene = synth.build_scene([synth.Tower(levels=3)], 0)
+    b = jb().Batch(scene, synth.params())
+    b.remove_block([0], [7])
+    b.apply_push([0], [1], [synth.AXIS_Y], [0.5], [20])
+    b.step(20)
+    act = b.active()
+    assert not act[7] and act.sum() == 8
+    for c in b.contacts(0):
+        assert 7 not in (c.a, c.b)
+    with pytest.raises(jb().JBError):
+        b.remove_block([0], [99])
+    with pytest.raises(jb().JBError):
+        b.apply_push([1], [0], [0], [0.1], [1])
