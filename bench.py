@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--max-steps", type=int, default=1 << 30, help="cap physics steps per episode")
     ap.add_argument("--tol", type=float, default=1e-5)
     ap.add_argument("--cap", type=int, default=20000)
+    ap.add_argument("--fixed-iters", type=int, default=0,
+                    help="fixed-sweep mode with this many sweeps per solve (profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-episodes", type=int, default=0)
@@ -71,6 +73,8 @@ def workload(args, rank):
         idx = np.linspace(0, E - 1, args.episodes).round().astype(int)
         scene, prot = synth.subset(scene, prot, idx)
     prm = dict(prm, residual_tol=args.tol, pgs_iter_cap=args.cap)
+    if args.fixed_iters:
+        prm = dict(prm, residual_tol=0.0, pgs_iters=args.fixed_iters)
     return scene, prot, prm
 
 
@@ -281,8 +285,9 @@ def main():
             "value": value, "unit": "body-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "450 episodes x 18-level towers, mu {0.25,0.40,0.60} x 150, removal rounds"
-                       if not args.episodes else f"{args.episodes} of the 450 episodes",
+            "config": {"workload": ("450 episodes x 18-level towers, mu {0.25,0.40,0.60} x 150, removal rounds"
+                                    if not args.episodes else f"{args.episodes} of the 450 episodes")
+                                   + (f", fixed {args.fixed_iters} sweeps (profiling)" if args.fixed_iters else ""),
                        "residual_tol": args.tol, "pgs_iter_cap": args.cap, "max_steps": args.max_steps,
                        "l2": "flushed (256 MB write) before every timed step",
                        "episodes": scene.n_episodes, "bodies": scene.n_bodies},
@@ -291,7 +296,10 @@ def main():
             "solver": {"sweeps_per_solve": float(st["total_sweeps"].sum() / max(st["solves"].sum(), 1)),
                        "not_converged_episodes": int(((st["status"] & jb.JB_EP_NOT_CONVERGED) != 0).sum()),
                        "collapsed": int(st["collapsed"].sum()), "body_steps_per_job": body_steps,
-                       "max_colours": int(st["max_colours"].max())}}
+                       "max_colours": int(st["max_colours"].max()),
+                       # critical path: job time over the busiest episode's sweeps
+                       "us_per_sweep_busiest_episode": ms / args.steps * 1e3 / float(st["total_sweeps"].max()),
+                       "fixed_iters": args.fixed_iters}}
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args, scene, prot, prm)
     if rank == 0:

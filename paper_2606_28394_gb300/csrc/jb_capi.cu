@@ -120,10 +120,10 @@ size_t carve(unsigned char* base, const Sizes& z, Dev& D, size_t* persist, int32
     c.nat_slot = a.take<uint32_t>(P);
     c.nat_pt = a.take<float>((size_t)P * kMaxPts * kNatPtFloats);
     c.nat_pf = a.take<float>((size_t)P * kNatPairFloats);
-    c.srt_f = a.take<float>((size_t)P * kSrtPairFloats);
+    c.srt_f = a.take<float>((size_t)P * kPairStride);
     c.srt_ab = a.take<uint32_t>(P);
     c.srt_np = a.take<int32_t>(P);
-    c.srt_pt = a.take<float>((size_t)P * kMaxPts * kSrtPtFloats);
+    c.srt_pt = a.take<float>((size_t)P * kPtStride);
   }
   if (persist) *persist = (a.off + 255) & ~size_t(255);
   D.work_counter = a.take<int32_t>(1);

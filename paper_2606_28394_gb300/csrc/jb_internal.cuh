@@ -16,7 +16,11 @@ constexpr int kMaxPts = 4;               // points per pair (Sec. 6.2.1, step d)
 constexpr int kNatPtFloats = 12;         // p[3], depth, local[3], lambda[3], pad[2]
 constexpr int kNatPairFloats = 8;        // n[3], depth_max, t1[3], mu
 constexpr int kSrtPairFloats = 8;        // n[3], t1[3], mu, depth_max
-constexpr int kSrtPtFloats = 10;         // p[3], invk[3], bias, lambda[3]
+constexpr int kSrtPtFloats = 13;         // p[3], 1/W_rr[3], W_01 W_02 W_12, bias, lambda[3]
+// Record strides of the colour-sorted arrays (record-major, odd strides so
+// that 32 lanes on consecutive slots hit 32 different banks).
+constexpr int kPairStride = kSrtPairFloats + 1;             // floats per pair header
+constexpr int kPtStride = kSrtPtFloats * kMaxPts + 1;       // floats per pair's points
 
 // body flags
 constexpr int kActive = 1;
@@ -66,10 +70,10 @@ struct ContactBuf {
   float* nat_pf;        // [P][kNatPairFloats]
   // colour-sorted solver arrays, used when a step's pairs exceed the
   // shared-memory capacity (stride Pc per field)
-  float* srt_f;         // per episode: [kSrtPairFloats][Pc]
+  float* srt_f;         // per episode: [Pc][kPairStride]
   uint32_t* srt_ab;     // local a | local b << 16 (ground = nb)
   int32_t* srt_np;
-  float* srt_pt;        // per episode: [kSrtPtFloats * 4][Pc]
+  float* srt_pt;        // per episode: [Pc][kPtStride], point k field f at k * 13 + f
 };
 
 struct Dev {
@@ -105,11 +109,12 @@ struct SmemPlan {
 };
 
 constexpr int kBodyFloats = 36;  // x3 q4 v3 w3 half3 R9 Iw6 ext3 invm mu
+constexpr int kBodyStride = kBodyFloats + 1;   // record-major, odd stride
 
 // Pairs of an episode whose solver arrays are kept in shared memory: an
 // intact tower needs about 3.6 per body.
 __host__ __device__ inline int smem_pairs(int nb_max, int pc_max) {
-  int p = (9 * nb_max) / 2 + 16;
+  int p = 4 * nb_max + 16;
   return p < pc_max ? p : pc_max;
 }
 
@@ -118,15 +123,15 @@ __host__ __device__ inline SmemPlan smem_plan(int nb_max, int pc_max, int ps) {
   s.nbs = nb_max + 1;
   int o = 0;
   s.off_mask = o; o += 8 * s.nbs;
-  s.off_f = o; o += 4 * kBodyFloats * s.nbs;
+  s.off_f = o; o += 4 * kBodyStride * s.nbs;
   s.off_flags = o; o += 4 * s.nbs;
   s.off_cand = o; o += 4 * cand_capacity(nb_max);
   s.off_col = o; o += 4 * 3 * (kMaxColours + 1);
   o = (o + 15) & ~15;
-  s.off_sf = o; o += 4 * kSrtPairFloats * ps;
+  s.off_sf = o; o += 4 * kPairStride * ps;
   s.off_ab = o; o += 4 * ps;
   s.off_np = o; o += 4 * ps;
-  s.off_sp = o; o += 4 * kSrtPtFloats * kMaxPts * ps;
+  s.off_sp = o; o += 4 * kPtStride * ps;
   o = (o + 15) & ~15;
   s.bytes = o;
   return s;

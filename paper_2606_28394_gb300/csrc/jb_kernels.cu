@@ -54,7 +54,7 @@ struct Sm {
   int32_t* np;
   float* sp;
   int ps;
-  __device__ __forceinline__ float& at(int f, int i) const { return F[f * nbs + i]; }
+  __device__ __forceinline__ float& at(int f, int i) const { return F[i * kBodyStride + f]; }
   __device__ __forceinline__ float3 ld3(int f, int i) const { return f3(at(f, i), at(f + 1, i), at(f + 2, i)); }
   __device__ __forceinline__ void st3(int f, int i, float3 v) const { at(f, i) = v.x; at(f + 1, i) = v.y; at(f + 2, i) = v.z; }
   // column k of the rotation matrix (body axis k in world coordinates)
@@ -398,8 +398,8 @@ __device__ __forceinline__ BufView buf_view(const Dev& D, int which, const Ep& E
   v.pf = b.nat_pf + E.poff * kNatPairFloats;
   v.ab = b.srt_ab + E.poff;
   v.np = b.srt_np + E.poff;
-  v.sf = b.srt_f + E.poff * kSrtPairFloats;
-  v.sp = b.srt_pt + E.poff * kMaxPts * kSrtPtFloats;
+  v.sf = b.srt_f + E.poff * kPairStride;
+  v.sp = b.srt_pt + E.poff * kPtStride;
   v.stride = E.Pc;
   return v;
 }
@@ -431,162 +431,239 @@ struct PairRegs {
   float3 va, wa, vb, wb, xa, xb, n, t1, t2;
   float ima, imb, mu;
   Sym3 Ia, Ib;
-  float3 rA[kMaxPts], rB[kMaxPts];
-  float ik[kMaxPts][3], bias[kMaxPts], lam[kMaxPts][3];
 };
 
-#define SP(f, k) B.sp[((f) * kMaxPts + (k)) * Pc + sl]
-#define SF(f) B.sf[(f) * Pc + sl]
+// The dynamic shared memory of the episode kernel.  Solver passes address it
+// through this symbol so that their loads and stores are shared-memory
+// accesses whatever the inlining.
+extern __shared__ __align__(16) unsigned char jb_smem[];
 
-__device__ __forceinline__ void load_pair(const Sm& s, const BufView& B, int Pc, int sl, PairRegs& R) {
-  uint32_t ab = B.ab[sl];
-  R.np = B.np[sl];
+// Where an episode's solver data lives: byte offsets into jb_smem for the body
+// records (kBodyStride floats each) and, when the step's pairs fit, for the colour-sorted
+// pair/point records (kPairStride, kPtStride); otherwise global pointers to them.
+struct SolverRef {
+  uint32_t oF, oflags, oab, onp, osf, osp;
+  const uint32_t* gab;
+  const int32_t* gnp;
+  const float* gsf;
+  float* gsp;
+  int nbs, S;
+  bool shared;
+};
+
+__device__ __forceinline__ SolverRef solver_ref(const Sm& s, const BufView& B) {
+  SolverRef r;
+  auto off = [](const void* p) { return (uint32_t)(reinterpret_cast<const unsigned char*>(p) - jb_smem); };
+  r.oF = off(s.F); r.oflags = off(s.flags);
+  r.shared = B.ab == s.ab;
+  r.oab = off(s.ab); r.onp = off(s.np); r.osf = off(s.sf); r.osp = off(s.sp);
+  r.gab = B.ab; r.gnp = B.np; r.gsf = B.sf; r.gsp = B.sp;
+  r.nbs = s.nbs; r.S = B.stride;
+  return r;
+}
+
+// Resolved pointers inside a solver function (shared or global sorted arrays).
+template <bool kShared>
+struct SolverView {
+  float* __restrict__ F;
+  const int* __restrict__ flags;
+  const uint32_t* __restrict__ ab;
+  const int32_t* __restrict__ np;
+  const float* __restrict__ sf;
+  float* __restrict__ sp;
+  int nbs, S;
+  __device__ __forceinline__ explicit SolverView(const SolverRef& r) {
+    F = reinterpret_cast<float*>(jb_smem + r.oF);
+    flags = reinterpret_cast<const int*>(jb_smem + r.oflags);
+    if constexpr (kShared) {
+      ab = reinterpret_cast<const uint32_t*>(jb_smem + r.oab);
+      np = reinterpret_cast<const int32_t*>(jb_smem + r.onp);
+      sf = reinterpret_cast<const float*>(jb_smem + r.osf);
+      sp = reinterpret_cast<float*>(jb_smem + r.osp);
+    } else {
+      ab = r.gab; np = r.gnp; sf = r.gsf; sp = r.gsp;
+    }
+    nbs = r.nbs; S = r.S;
+  }
+};
+
+#define VF(f, i) V.F[(i) * kBodyStride + (f)]
+#define VSP(f, k) V.sp[sl * kPtStride + (k) * kSrtPtFloats + (f)]
+#define VSF(f) V.sf[sl * kPairStride + (f)]
+
+template <bool kS>
+__device__ __forceinline__ float3 vld3(const SolverView<kS>& V, int f, int i) {
+  return f3(VF(f, i), VF(f + 1, i), VF(f + 2, i));
+}
+template <bool kS>
+__device__ __forceinline__ void vst3(const SolverView<kS>& V, int f, int i, float3 x) {
+  VF(f, i) = x.x; VF(f + 1, i) = x.y; VF(f + 2, i) = x.z;
+}
+
+template <bool kS>
+__device__ __forceinline__ void load_pair(const SolverView<kS>& V, int sl, PairRegs& R) {
+  uint32_t ab = V.ab[sl];
+  R.np = V.np[sl];
   R.a = ab & 0xffff; R.b = ab >> 16;
-  R.n = f3(SF(0), SF(1), SF(2));
-  R.t1 = f3(SF(3), SF(4), SF(5));
+  R.n = f3(VSF(0), VSF(1), VSF(2));
+  R.t1 = f3(VSF(3), VSF(4), VSF(5));
   R.t2 = cross(R.n, R.t1);
-  R.mu = SF(6);
-  R.va = s.ld3(FV, R.a); R.wa = s.ld3(FW, R.a);
-  R.vb = s.ld3(FV, R.b); R.wb = s.ld3(FW, R.b);
-  R.xa = s.ld3(FX, R.a); R.xb = s.ld3(FX, R.b);
-  R.ima = s.at(FM, R.a); R.imb = s.at(FM, R.b);
-  R.Ia = ld_iw(s, R.a); R.Ib = ld_iw(s, R.b);
-  R.da = !(s.flags[R.a] & kStatic);
-  R.db = !(s.flags[R.b] & kStatic);
+  R.mu = VSF(6);
+  R.va = vld3(V, FV, R.a); R.wa = vld3(V, FW, R.a);
+  R.vb = vld3(V, FV, R.b); R.wb = vld3(V, FW, R.b);
+  R.xa = vld3(V, FX, R.a); R.xb = vld3(V, FX, R.b);
+  R.ima = VF(FM, R.a); R.imb = VF(FM, R.b);
+  R.Ia.xx = VF(FI, R.a); R.Ia.yy = VF(FI + 1, R.a); R.Ia.zz = VF(FI + 2, R.a);
+  R.Ia.xy = VF(FI + 3, R.a); R.Ia.xz = VF(FI + 4, R.a); R.Ia.yz = VF(FI + 5, R.a);
+  R.Ib.xx = VF(FI, R.b); R.Ib.yy = VF(FI + 1, R.b); R.Ib.zz = VF(FI + 2, R.b);
+  R.Ib.xy = VF(FI + 3, R.b); R.Ib.xz = VF(FI + 4, R.b); R.Ib.yz = VF(FI + 5, R.b);
+  R.da = !(V.flags[R.a] & kStatic);
+  R.db = !(V.flags[R.b] & kStatic);
 }
 
-// point k: lever arms from the stored contact point, inverse effective masses,
-// bias and impulses
-__device__ __forceinline__ void load_point(const BufView& B, int Pc, int sl, int k, PairRegs& R) {
-  float3 p = f3(SP(0, k), SP(1, k), SP(2, k));
-  R.rA[k] = p - R.xa;
-  R.rB[k] = p - R.xb;
-  R.ik[k][0] = SP(3, k); R.ik[k][1] = SP(4, k); R.ik[k][2] = SP(5, k);
-  R.bias[k] = SP(6, k);
-  R.lam[k][0] = SP(7, k); R.lam[k][1] = SP(8, k); R.lam[k][2] = SP(9, k);
+// Velocity of B relative to A at the point (lever arms rA, rB).
+__device__ __forceinline__ float3 point_rel_vel(const PairRegs& R, float3 rA, float3 rB) {
+  return (R.vb + cross(R.wb, rB)) - (R.va + cross(R.wa, rA));
 }
 
-// One constraint row: impulse change dl along d at lever arms (rA, rB).
-__device__ __forceinline__ void row_apply(PairRegs& R, float3 d, float3 ia, float3 ib, float dl) {
-  R.va = R.va - (R.ima * dl) * d;
-  R.vb = R.vb + (R.imb * dl) * d;
-  R.wa = R.wa - dl * ia;
-  R.wb = R.wb + dl * ib;
+// Applies the impulse P at the point: A gets -P, B gets +P (linear and angular).
+__device__ __forceinline__ void apply_point(PairRegs& R, float3 rA, float3 rB, float3 P) {
+  R.va = R.va - R.ima * P;
+  R.vb = R.vb + R.imb * P;
+  R.wa = R.wa - mul(R.Ia, cross(rA, P));
+  R.wb = R.wb + mul(R.Ib, cross(rB, P));
 }
 
 // mode 0: apply warm-start impulses; mode 1: one Gauss-Seidel pass over the
-// pair's points, rows n, t1, t2 (Eq. lambda_n with the listing's (1+e)
-// factor, Eq. coulomb_pgs box clip with the just-updated normal impulse);
-// mode 2: position correction (Eq. baumgarte, translation only).
-template <int mode>
-__device__ __forceinline__ void pair_pass(const Sm& s, const BufView& B, int Pc, int sl, const Params& Pm) {
+// pair's points, rows n, t1, t2 in order (Eq. lambda_n with the listing's
+// (1+e) factor, Eq. coulomb_pgs box clip with the just-updated normal
+// impulse); mode 2: position correction (Eq. baumgarte, translation only).
+//
+// Within a point the three rows act at the same lever arms, so the change of
+// the point's relative velocity after an impulse change dl along d_s is
+// W d_s dl, with W the 3x3 inverse effective mass in the contact frame
+// (diagonal: Eq. keff).  The rows therefore run on the three scalar
+// velocities and the bodies take the point's summed impulse once: the same
+// Gauss-Seidel iterate as updating the bodies after every row.
+template <int mode, bool kS>
+__device__ __forceinline__ void pair_pass(const SolverView<kS>& V, int sl, float e1, float beta, float slop) {
   if constexpr (mode == 2) {
-    uint32_t ab = B.ab[sl];
+    uint32_t ab = V.ab[sl];
     int a = ab & 0xffff, b = ab >> 16;
-    float3 n = f3(SF(0), SF(1), SF(2));
-    float pen = SF(7) - Pm.slop;
-    float ima = s.at(FM, a), imb = s.at(FM, b);
+    float3 n = f3(VSF(0), VSF(1), VSF(2));
+    float pen = VSF(7) - slop;
+    float ima = VF(FM, a), imb = VF(FM, b);
     float wsum = ima + imb;
     if (pen > 0.f && wsum > 0.f) {
-      float c = Pm.beta * pen / wsum;
-      if (!(s.flags[a] & kStatic)) s.st3(FX, a, s.ld3(FX, a) - (c * ima) * n);
-      if (!(s.flags[b] & kStatic)) s.st3(FX, b, s.ld3(FX, b) + (c * imb) * n);
+      float c = beta * pen / wsum;
+      if (!(V.flags[a] & kStatic)) vst3(V, FX, a, vld3(V, FX, a) - (c * ima) * n);
+      if (!(V.flags[b] & kStatic)) vst3(V, FX, b, vld3(V, FX, b) + (c * imb) * n);
     }
     return;
   }
   PairRegs R;
-  load_pair(s, B, Pc, sl, R);
-  const float e1 = 1.f + Pm.restitution;
+  load_pair(V, sl, R);
 #pragma unroll
   for (int k = 0; k < kMaxPts; ++k) {
     if (k >= R.np) break;
-    load_point(B, Pc, sl, k, R);
+    const float3 p = f3(VSP(0, k), VSP(1, k), VSP(2, k));
+    const float3 rA = p - R.xa, rB = p - R.xb;
+    float l0 = VSP(10, k), l1 = VSP(11, k), l2 = VSP(12, k);
     if constexpr (mode == 0) {
-      float3 Pv = R.lam[k][0] * R.n + R.lam[k][1] * R.t1 + R.lam[k][2] * R.t2;
-      R.va = R.va - R.ima * Pv;
-      R.vb = R.vb + R.imb * Pv;
-      R.wa = R.wa - mul(R.Ia, cross(R.rA[k], Pv));
-      R.wb = R.wb + mul(R.Ib, cross(R.rB[k], Pv));
+      apply_point(R, rA, rB, l0 * R.n + l1 * R.t1 + l2 * R.t2);
     } else {
-    const float3 rA = R.rA[k], rB = R.rB[k];
-    // the angular Jacobian terms and M^-1 J^T do not depend on the velocities
-    const float3 can = cross(rA, R.n), cbn = cross(rB, R.n);
-    const float3 ca1 = cross(rA, R.t1), cb1 = cross(rB, R.t1);
-    const float3 ca2 = cross(rA, R.t2), cb2 = cross(rB, R.t2);
-    const float3 ian = mul(R.Ia, can), ibn = mul(R.Ib, cbn);
-    const float3 ia1 = mul(R.Ia, ca1), ib1 = mul(R.Ib, cb1);
-    const float3 ia2 = mul(R.Ia, ca2), ib2 = mul(R.Ib, cb2);
-    float l0 = R.lam[k][0], l1 = R.lam[k][1], l2 = R.lam[k][2];
-    float vn = dot(R.vb - R.va, R.n) + dot(R.wb, cbn) - dot(R.wa, can);
-    float nl0 = fmaxf(0.f, l0 - e1 * (vn + R.bias[k]) * R.ik[k][0]);
-    row_apply(R, R.n, ian, ibn, nl0 - l0);
-    float lim = R.mu * nl0;
-    float v1 = dot(R.vb - R.va, R.t1) + dot(R.wb, cb1) - dot(R.wa, ca1);
-    float nl1 = fminf(fmaxf(l1 - v1 * R.ik[k][1], -lim), lim);
-    row_apply(R, R.t1, ia1, ib1, nl1 - l1);
-    float v2 = dot(R.vb - R.va, R.t2) + dot(R.wb, cb2) - dot(R.wa, ca2);
-    float nl2 = fminf(fmaxf(l2 - v2 * R.ik[k][2], -lim), lim);
-    row_apply(R, R.t2, ia2, ib2, nl2 - l2);
-    SP(7, k) = nl0; SP(8, k) = nl1; SP(9, k) = nl2;
+      const float ik0 = VSP(3, k), ik1 = VSP(4, k), ik2 = VSP(5, k);
+      const float w01 = VSP(6, k), w02 = VSP(7, k), w12 = VSP(8, k);
+      const float bias = VSP(9, k);
+      const float3 u = point_rel_vel(R, rA, rB);
+      float vn = dot(u, R.n), v1 = dot(u, R.t1), v2 = dot(u, R.t2);
+      float nl0 = fmaxf(0.f, l0 - e1 * (vn + bias) * ik0);
+      float d0 = nl0 - l0;
+      v1 += w01 * d0;
+      v2 += w02 * d0;
+      float lim = R.mu * nl0;
+      float nl1 = fminf(fmaxf(l1 - v1 * ik1, -lim), lim);
+      float d1 = nl1 - l1;
+      v2 += w12 * d1;
+      float nl2 = fminf(fmaxf(l2 - v2 * ik2, -lim), lim);
+      float d2 = nl2 - l2;
+      apply_point(R, rA, rB, d0 * R.n + d1 * R.t1 + d2 * R.t2);
+      VSP(10, k) = nl0; VSP(11, k) = nl1; VSP(12, k) = nl2;
     }
   }
-  if (R.da) { s.st3(FV, R.a, R.va); s.st3(FW, R.a, R.wa); }
-  if (R.db) { s.st3(FV, R.b, R.vb); s.st3(FW, R.b, R.wb); }
+  if (R.da) { vst3(V, FV, R.a, R.va); vst3(V, FW, R.a, R.wa); }
+  if (R.db) { vst3(V, FV, R.b, R.vb); vst3(V, FW, R.b, R.wb); }
 }
 
 // Residual of one pair at the current state (no update): max over rows of
 // k |proj(lambda - (v + b) / k) - lambda|, k the inverse effective mass.
-__device__ __forceinline__ float pair_residual(const Sm& s, const BufView& B, int Pc, int sl) {
+template <bool kS>
+__device__ __forceinline__ float pair_residual(const SolverView<kS>& V, int sl) {
   PairRegs R;
-  load_pair(s, B, Pc, sl, R);
+  load_pair(V, sl, R);
   float r = 0.f;
 #pragma unroll
   for (int k = 0; k < kMaxPts; ++k) {
     if (k >= R.np) break;
-    load_point(B, Pc, sl, k, R);
-    const float3 rA = R.rA[k], rB = R.rB[k];
-    float3 dv = R.vb - R.va;
-    float vn = dot(dv, R.n) + dot(R.wb, cross(rB, R.n)) - dot(R.wa, cross(rA, R.n));
-    float v1 = dot(dv, R.t1) + dot(R.wb, cross(rB, R.t1)) - dot(R.wa, cross(rA, R.t1));
-    float v2 = dot(dv, R.t2) + dot(R.wb, cross(rB, R.t2)) - dot(R.wa, cross(rA, R.t2));
-    float l0 = R.lam[k][0], l1 = R.lam[k][1], l2 = R.lam[k][2];
+    const float3 p = f3(VSP(0, k), VSP(1, k), VSP(2, k));
+    const float3 u = point_rel_vel(R, p - R.xa, p - R.xb);
+    const float ik0 = VSP(3, k), ik1 = VSP(4, k), ik2 = VSP(5, k), bias = VSP(9, k);
+    const float l0 = VSP(10, k), l1 = VSP(11, k), l2 = VSP(12, k);
     float lim = R.mu * l0;
-    float p0 = fmaxf(0.f, l0 - (vn + R.bias[k]) * R.ik[k][0]);
-    float p1 = fminf(fmaxf(l1 - v1 * R.ik[k][1], -lim), lim);
-    float p2 = fminf(fmaxf(l2 - v2 * R.ik[k][2], -lim), lim);
-    float m = fmaxf(fabsf(p0 - l0) / R.ik[k][0], fmaxf(fabsf(p1 - l1) / R.ik[k][1], fabsf(p2 - l2) / R.ik[k][2]));
+    float p0 = fmaxf(0.f, l0 - (dot(u, R.n) + bias) * ik0);
+    float p1 = fminf(fmaxf(l1 - dot(u, R.t1) * ik1, -lim), lim);
+    float p2 = fminf(fmaxf(l2 - dot(u, R.t2) * ik2, -lim), lim);
+    float m = fmaxf(fabsf(p0 - l0) / ik0, fmaxf(fabsf(p1 - l1) / ik1, fabsf(p2 - l2) / ik2));
     if (!(m <= r)) r = m;   // keeps NaN
   }
   return r;
 }
-#undef SP
-#undef SF
+#undef VSP
+#undef VSF
 
 // Residual of the whole episode (warp max; NaN propagates).
-__device__ __noinline__ float episode_residual(const Sm& s, const BufView& B, int Pc, int npairs, int lane) {
-  float r = 0.f;
+template <bool kS>
+__device__ __noinline__ float episode_residual_t(const SolverRef r, int npairs, int lane) {
+  const SolverView<kS> V(r);
+  float res = 0.f;
   for (int sl = lane; sl < npairs; sl += 32) {
-    float m = pair_residual(s, B, Pc, sl);
-    if (!(m <= r)) r = m;
+    float m = pair_residual(V, sl);
+    if (!(m <= res)) res = m;
   }
-  bool nan = __any_sync(FULL, !(r == r));
-  return nan ? __int_as_float(0x7fc00000) : warp_max(r);
+  bool nan = __any_sync(FULL, !(res == res));
+  return nan ? __int_as_float(0x7fc00000) : warp_max(res);
 }
 
 // Runs `mode` over every colour in order; lanes take the slots of a colour.
-template <int mode>
-__device__ __noinline__ void colour_passes(const Sm& s, const BufView& B, int Pc, int ncol, int lane, const Params& Pm) {
+// `off` holds the colour offsets (ncol + 1 entries).
+template <int mode, bool kS>
+__device__ __noinline__ void colour_passes_t(const SolverRef r, const int* __restrict__ off, int ncol, int lane,
+                                             float e1, float beta, float slop) {
+  const SolverView<kS> V(r);
   for (int c = 0; c < ncol; ++c) {
-    int s0 = s.off[c], s1 = s.off[c + 1];
+    int s0 = off[c], s1 = off[c + 1];
     if (c == kSerial) {
       if (lane == 0)
-        for (int sl = s0; sl < s1; ++sl) pair_pass<mode>(s, B, Pc, sl, Pm);
+        for (int sl = s0; sl < s1; ++sl) pair_pass<mode>(V, sl, e1, beta, slop);
     } else {
-      for (int sl = s0 + lane; sl < s1; sl += 32) pair_pass<mode>(s, B, Pc, sl, Pm);
+      for (int sl = s0 + lane; sl < s1; sl += 32) pair_pass<mode>(V, sl, e1, beta, slop);
     }
     __syncwarp();
   }
 }
+
+template <int mode>
+__device__ __forceinline__ void colour_passes(const SolverRef& r, const int* off, int ncol, int lane, float e1,
+                                              float beta, float slop) {
+  if (r.shared) colour_passes_t<mode, true>(r, off, ncol, lane, e1, beta, slop);
+  else colour_passes_t<mode, false>(r, off, ncol, lane, e1, beta, slop);
+}
+
+__device__ __forceinline__ float episode_residual(const SolverRef& r, int npairs, int lane) {
+  return r.shared ? episode_residual_t<true>(r, npairs, lane) : episode_residual_t<false>(r, npairs, lane);
+}
+
+#undef VF
 
 // ------------------------------------------------------------------ substep
 struct StepOut {
@@ -845,7 +922,6 @@ __device__ StepOut substep(const Dev& D, const Ep& E, EpState& st, float h) {
   // (7) contact setup (Eq. keff) into the colour-sorted solver arrays:
   // shared memory when the pairs fit, else this buffer's global copy
   if (npairs <= s.ps) use_smem_solver(Bc, s);
-  const int S = Bc.stride;
   const float ih = 1.f / h;
   for (int p = lane; p < npairs; p += 32) {
     uint32_t key = Bc.key[p];
@@ -864,38 +940,48 @@ __device__ StepOut substep(const Dev& D, const Ep& E, EpState& st, float h) {
     pf[4] = t1.x; pf[5] = t1.y; pf[6] = t1.z; pf[7] = mu;
     float* sf = Bc.sf;
     float* sp = Bc.sp;
-    sf[0 * S + sl] = n.x; sf[1 * S + sl] = n.y; sf[2 * S + sl] = n.z;
-    sf[3 * S + sl] = t1.x; sf[4 * S + sl] = t1.y; sf[5 * S + sl] = t1.z;
-    sf[6 * S + sl] = mu; sf[7 * S + sl] = dmax;
+    float* hf = sf + sl * kPairStride;
+    hf[0] = n.x; hf[1] = n.y; hf[2] = n.z;
+    hf[3] = t1.x; hf[4] = t1.y; hf[5] = t1.z;
+    hf[6] = mu; hf[7] = dmax;
     Bc.ab[sl] = (uint32_t)ia | ((uint32_t)b << 16);
     Bc.np[sl] = np;
     float3 xa = s.ld3(FX, ia), xb = s.ld3(FX, b);
     float ima = s.at(FM, ia), imb = s.at(FM, b);
+    const Sym3 Ia = ld_iw(s, ia), Ib = ld_iw(s, b);
     for (int k = 0; k < np; ++k) {
       const float* q = pt + k * kNatPtFloats;
       float3 pp = f3(q[0], q[1], q[2]);
       float3 rA = pp - xa, rB = pp - xb;
-      float3 dirs[3] = {n, t1, t2};
-      float ik[3];
-#pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        float3 ca = cross(rA, dirs[r]), cb = cross(rB, dirs[r]);
-        float kk = ima + imb + dot(ca, s.iw_mul(ia, ca)) + dot(cb, s.iw_mul(b, cb));
-        ik[r] = 1.f / kk;
-      }
+      // W_rs = d_r . K d_s, K the point's inverse mass matrix; the diagonal
+      // is Eq. keff for the rows n, t1, t2
+      float3 ca0 = cross(rA, n), ca1 = cross(rA, t1), ca2 = cross(rA, t2);
+      float3 cb0 = cross(rB, n), cb1 = cross(rB, t1), cb2 = cross(rB, t2);
+      float3 ia0 = mul(Ia, ca0), ia1 = mul(Ia, ca1), ia2 = mul(Ia, ca2);
+      float3 ib0 = mul(Ib, cb0), ib1 = mul(Ib, cb1), ib2 = mul(Ib, cb2);
+      float lin = ima + imb;
+      float w00 = lin + dot(ca0, ia0) + dot(cb0, ib0);
+      float w11 = lin + dot(ca1, ia1) + dot(cb1, ib1);
+      float w22 = lin + dot(ca2, ia2) + dot(cb2, ib2);
+      float w01 = dot(ca0, ia1) + dot(cb0, ib1);
+      float w02 = dot(ca0, ia2) + dot(cb0, ib2);
+      float w12 = dot(ca1, ia2) + dot(cb1, ib2);
       float dep = q[3];
       float bias = dep < 0.f ? -dep * ih : 0.f;
-#define W(f, v) sp[((f) * kMaxPts + k) * S + sl] = (v)
+#define W(f, v) sp[sl * kPtStride + k * kSrtPtFloats + (f)] = (v)
       W(0, pp.x); W(1, pp.y); W(2, pp.z);
-      W(3, ik[0]); W(4, ik[1]); W(5, ik[2]); W(6, bias);
-      W(7, q[7]); W(8, q[8]); W(9, q[9]);
+      W(3, 1.f / w00); W(4, 1.f / w11); W(5, 1.f / w22);
+      W(6, w01); W(7, w02); W(8, w12); W(9, bias);
+      W(10, q[7]); W(11, q[8]); W(12, q[9]);
 #undef W
     }
   }
   __syncwarp();
 
   // (8) warm start: apply the inherited impulses
-  if (Pm.warm_start == 1) colour_passes<0>(s, Bc, S, ncol, lane, Pm);
+  const SolverRef V = solver_ref(s, Bc);
+  const float e1 = 1.f + Pm.restitution;
+  if (Pm.warm_start == 1) colour_passes<0>(V, s.off, ncol, lane, e1, Pm.beta, Pm.slop);
 
   // (9) projected Gauss-Seidel sweeps
   int sweeps = 0;
@@ -905,12 +991,12 @@ __device__ StepOut substep(const Dev& D, const Ep& E, EpState& st, float h) {
     const int cap = rmode ? Pm.pgs_iter_cap : Pm.pgs_iters;
     const int every = Pm.residual_every > 0 ? Pm.residual_every : 1;
     while (sweeps < cap) {
-      colour_passes<1>(s, Bc, S, ncol, lane, Pm);
+      colour_passes<1>(V, s.off, ncol, lane, e1, Pm.beta, Pm.slop);
       ++sweeps;
       bool check = rmode ? (sweeps >= Pm.pgs_min_iters && ((sweeps - Pm.pgs_min_iters) % every == 0 || sweeps == cap))
                          : (sweeps == cap);
       if (check) {
-        res = episode_residual(s, Bc, S, npairs, lane);
+        res = episode_residual(V, npairs, lane);
         if (rmode && (res <= Pm.residual_tol || !(res == res))) break;
       }
     }
@@ -923,9 +1009,8 @@ __device__ StepOut substep(const Dev& D, const Ep& E, EpState& st, float h) {
     float* pt = Bc.pt + (size_t)p * kMaxPts * kNatPtFloats;
     for (int k = 0; k < np; ++k) {
       float* q = pt + k * kNatPtFloats;
-      q[7] = Bc.sp[(7 * kMaxPts + k) * S + sl];
-      q[8] = Bc.sp[(8 * kMaxPts + k) * S + sl];
-      q[9] = Bc.sp[(9 * kMaxPts + k) * S + sl];
+      const float* rec = Bc.sp + sl * kPtStride + k * kSrtPtFloats;
+      q[7] = rec[10]; q[8] = rec[11]; q[9] = rec[12];
     }
   }
 
@@ -949,7 +1034,7 @@ __device__ StepOut substep(const Dev& D, const Ep& E, EpState& st, float h) {
   __syncwarp();
 
   // (11) position correction (Eq. baumgarte), colour by colour
-  colour_passes<2>(s, Bc, S, ncol, lane, Pm);
+  colour_passes<2>(V, s.off, ncol, lane, e1, Pm.beta, Pm.slop);
 
   st.cur = cur;
   st.npairs = npairs;
@@ -1177,9 +1262,8 @@ __device__ void run_episode(const Dev& D, int e, int mode, int max_steps, unsign
 
 // Persistent grid: each warp claims episodes from the work counter.
 __global__ void __launch_bounds__(kWarpsPerCta * 32) episode_kernel(Dev D, int mode, int max_steps) {
-  extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned char* base = smem + (size_t)warp * D.smem_per_warp;
+  unsigned char* base = jb_smem + (size_t)warp * D.smem_per_warp;
   for (;;) {
     int idx = 0;
     if (lane == 0) idx = atomicAdd(D.work_counter, 1);
