@@ -805,7 +805,7 @@ __device__ StepOut substep(const Dev& D, const Ep& E, EpState& st, float h) {
   }
   __syncwarp();
 
-  // (4) warm-start matching and colour inheritance against the previous step
+  // (4) warm-start matching against the previous step
   const int nprev = st.npairs;
   const float mr2 = Pm.match_radius * Pm.match_radius;
   for (int p = lane; p < npairs; p += 32) {
@@ -817,10 +817,7 @@ __device__ StepOut substep(const Dev& D, const Ep& E, EpState& st, float h) {
       if (km == key) { q = mid; break; }
       if (km < key) lo = mid + 1; else hi = mid - 1;
     }
-    if (q < 0) continue;
-    uint32_t qs = Bp.slot[q];
-    Bc.slot[p] = (qs & 0xffff0000u);
-    if (Pm.warm_start != 1) continue;
+    if (q < 0 || Pm.warm_start != 1) continue;
     uint32_t fn = Bc.feat[p], fo = Bp.feat[q];
     if (((fn ^ fo) & 0x00ffff00u) != 0) continue;
     int npn = fn >> 24, npo = fo >> 24;
@@ -844,47 +841,63 @@ __device__ StepOut substep(const Dev& D, const Ep& E, EpState& st, float h) {
   }
   __syncwarp();
 
-  // (5) colouring: inherited colours claim their bits, new pairs greedily
+  // (5) colouring, redone every step: greedy (lowest colour free at both
+  // dynamic bodies) over the pairs in order of key = (contact height in 1 mm
+  // bins ascending, natural index descending).  The colours are swept in
+  // index order, so lower contacts tend to be solved first; on 18-level
+  // towers this order needs several times fewer sweeps to reach a residual
+  // tolerance than colouring in natural order, at the same colour count.
+  // The candidate array (free after the narrowphase) holds the order.
+  uint32_t* ord = s.cand;
+  {
+    const int nchunk = (npairs + 31) / 32;
+    for (int p0 = 0; p0 < npairs; p0 += 32) {
+      int p = p0 + lane;
+      uint32_t key = 0xffffffffu;
+      if (p < npairs) {
+        float z = Bc.pt[(size_t)p * kMaxPts * kNatPtFloats + 2];
+        int bin = (int)floorf((z + 5e-4f) * 1000.f);
+        bin = min(max(bin + 1, 0), 65535);
+        key = ((uint32_t)bin << 16) | (uint32_t)(0xffff - p);
+      }
+      // rank among all pairs: keys are distinct
+      int rank = 0;
+      for (int c = 0; c < nchunk; ++c) {
+        int q = c * 32 + lane;
+        uint32_t kq = 0xffffffffu;
+        if (q < npairs) {
+          float zq = Bc.pt[(size_t)q * kMaxPts * kNatPtFloats + 2];
+          int bq = (int)floorf((zq + 5e-4f) * 1000.f);
+          bq = min(max(bq + 1, 0), 65535);
+          kq = ((uint32_t)bq << 16) | (uint32_t)(0xffff - q);
+        }
+        for (int j = 0; j < 32; ++j) rank += __shfl_sync(FULL, kq, j) < key;
+      }
+      if (p < npairs) ord[rank] = (uint32_t)p;
+    }
+  }
   for (int i = lane; i <= nb; i += 32) s.mask[i] = 0ull;
   __syncwarp();
-  for (int p = lane; p < npairs; p += 32) {
+  bool many = false;
+  for (int t = 0; t < npairs; ++t) {
+    int p = ord[t];
     uint32_t key = Bc.key[p];
-    int col = Bc.slot[p] >> 16;
-    if (col >= kSerial) continue;
     int a = (int)(key >> 16) - 1, b = (int)(key & 0xffff);
-    unsigned long long bit = 1ull << col;
-    if (a >= 0 && !(s.flags[a] & kStatic)) atomicOr(&s.mask[a], bit);
-    if (!(s.flags[b] & kStatic)) atomicOr(&s.mask[b], bit);
-  }
-  __syncwarp();
-  for (int p0 = 0; p0 < npairs; p0 += 32) {
-    int p = p0 + lane;
-    int col = 0, a = 0, b = 0;
-    if (p < npairs) {
-      uint32_t key = Bc.key[p];
-      col = Bc.slot[p] >> 16;
-      a = (int)(key >> 16) - 1;
-      b = (int)(key & 0xffff);
-    }
-    unsigned todo = __ballot_sync(FULL, p < npairs && col == 0xffff);
-    while (todo) {
-      int j = __ffs(todo) - 1;
-      todo &= todo - 1;
-      int aj = __shfl_sync(FULL, a, j), bj = __shfl_sync(FULL, b, j);
-      bool sa = aj < 0 || (s.flags[aj] & kStatic), sb = (s.flags[bj] & kStatic);
-      unsigned long long m = (sa ? 0ull : s.mask[aj]) | (sb ? 0ull : s.mask[bj]);
-      int c = __ffsll((long long)~m) - 1;
-      if (c < 0 || c >= kSerial) c = kSerial;
-      __syncwarp();
-      if (lane == 0 && c < kSerial) {
-        if (!sa) s.mask[aj] |= 1ull << c;
-        if (!sb) s.mask[bj] |= 1ull << c;
+    bool sa = a < 0 || (s.flags[a] & kStatic), sb = (s.flags[b] & kStatic);
+    unsigned long long m = (sa ? 0ull : s.mask[a]) | (sb ? 0ull : s.mask[b]);
+    int c = __ffsll((long long)~m) - 1;
+    if (c < 0 || c >= kSerial) { c = kSerial; many = true; }
+    __syncwarp();
+    if (lane == 0) {
+      if (c < kSerial) {
+        if (!sa) s.mask[a] |= 1ull << c;
+        if (!sb) s.mask[b] |= 1ull << c;
       }
-      if (lane == j) col = c;
-      __syncwarp();
+      Bc.slot[p] = (uint32_t)c << 16;
     }
-    if (p < npairs) Bc.slot[p] = (uint32_t)col << 16;
+    __syncwarp();
   }
+  if (many) out.status |= JB_EP_TOO_MANY_COLOURS;
   __syncwarp();
 
   // (6) counting sort by colour (ascending natural index within a colour)
