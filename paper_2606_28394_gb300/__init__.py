@@ -173,7 +173,7 @@ class Batch:
     The workspace is a torch uint8 tensor sized by jb_workspace_bytes; work is
     queued on ``stream`` (default: torch's current stream)."""
 
-    def __init__(self, scene, params, max_moves=0, stream=None, device=None):
+    def __init__(self, scene, params, max_moves=0, stream=None, device=None, workspace=None):
         import torch
         self.torch = torch
         self.device = torch.device(device or "cuda")
@@ -191,7 +191,10 @@ class Batch:
         if nbytes == 0:
             raise JBError(JB_EINVAL, "jb_workspace_bytes")
         with torch.cuda.device(self.device):
-            self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+            if workspace is not None and workspace.numel() >= nbytes + 256 and workspace.is_cuda:
+                self.workspace = workspace
+            else:
+                self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
             self.stream = stream or torch.cuda.current_stream(self.device)
         ptr = self.workspace.data_ptr()
         self._ws_ptr = (ptr + 255) & ~255
