@@ -10,7 +10,12 @@ Tolerances:
     normals within 1e-5;
   - one step from an identical state with both solvers converged to a PGS
     residual <= 1e-5 m/s: positions within 1e-5 m, velocities within 1e-4 m/s
-    (angular velocity scaled by the block's half diagonal).
+    (angular velocity scaled by the block's half diagonal).  The residual
+    bounds the relative velocity at each contact; a body's velocity adds those
+    along its chain of contacts to the ground, so on an n-level stack two
+    solutions at residual tol may differ by up to ~2 n tol.  The parity cases
+    therefore converge both solvers to 1e-6 (which is <= 1e-5), giving
+    2 * 18 * 1e-6 < 1e-4 on the 18-level tower.
 """
 import math
 
@@ -141,7 +146,7 @@ def velocity_error(scene, v1, w1, v2, w2):
     return np.max(np.abs(v1 - v2)), np.max(np.abs(w1 - w2).max(0) * diag)
 
 
-@pytest.mark.parametrize("name,tol", [("tower4_perturbed", 1e-5), ("pile", 1e-5), ("tower18", 1e-5)])
+@pytest.mark.parametrize("name,tol", [("tower4_perturbed", 1e-6), ("pile", 1e-6), ("tower18", 1e-6)])
 def test_one_step_converged_parity(cuda_device, name, tol):
     if name == "tower4_perturbed":
         scene = synth.perturbed(synth.build_scene([synth.Tower(levels=4, mu=0.5)], 1), 5, dx=2e-4, dang=0.01)
@@ -149,7 +154,7 @@ def test_one_step_converged_parity(cuda_device, name, tol):
         scene = synth.pile_scene(28, seed=5)
     else:
         scene = synth.build_scene([synth.Tower()], 0)
-    prm = synth.params(residual_tol=tol, pgs_iter_cap=100000)
+    prm = synth.params(residual_tol=tol, pgs_iter_cap=200000)
     b, w = step_both(scene, prm)
     st = b.stats()
     assert st["status"][0] == 0 and st["last_residual"][0] <= tol
