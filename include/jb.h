@@ -250,6 +250,39 @@ size_t jb_state_bytes(const jb_batch* b);
 jb_status jb_save_state(jb_batch* b, void* host_buf, size_t bytes);
 jb_status jb_load_state(jb_batch* b, const void* host_buf, size_t bytes);
 
+/* Stepping for callers that cannot allocate device memory.
+ *
+ * Not part of the paper's method (the paper has no counterpart): an
+ * allocation-free variant of jb_batch_create + jb_step for code that runs
+ * where device allocation is unavailable or forbidden -- inside a memory pool
+ * owned by another framework, in a real-time loop that must not call
+ * cudaMalloc, or in a process whose allocator is locked.  It advances
+ * n_episodes independent episodes by n_steps host-driven steps (gravity and
+ * contacts only; no pushes or schedule), starting with an empty warm-start
+ * cache, and writes the new state back in place.
+ *
+ * Arguments: body_off is a HOST array [n_episodes + 1]; every other array is
+ * DEVICE memory in the layout of jb_scene ([3][B], [4][B], [B], [E]); d_x,
+ * d_q, d_v, d_w are read and overwritten.  Work is queued on cuda_stream and
+ * the call returns without synchronising; the caller synchronises before
+ * reading the outputs.
+ *
+ * Scratch: the library's file-scope device array of JB_NOALLOC_SCRATCH_BYTES
+ * (32 MiB; every GPU that loads the library holds it until the process
+ * exits).  A batch whose layout needs more returns JB_ENOMEM with the sizes
+ * in jb_last_error() and launches nothing.  The call makes no device memory
+ * allocation and frees nothing.  Its first call on a device looks up the
+ * scratch address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  All calls share the one array, which keeps the last call's
+ * contents (each call re-initialises what must start at zero): calls that
+ * overlap on the GPU (different streams, or different host threads) race.
+ */
+#define JB_NOALLOC_SCRATCH_BYTES (32u << 20)
+jb_status jb_step_noalloc(int32_t n_episodes, const int32_t* body_off, const float* d_half,
+                          const float* d_mass, const float* d_mu, const float* d_ground_mu,
+                          float* d_x, float* d_q, float* d_v, float* d_w,
+                          const jb_solver_params* p, int32_t n_steps, void* cuda_stream);
+
 const char* jb_status_str(jb_status s);
 const char* jb_last_error(void);
 const char* jb_version(void);

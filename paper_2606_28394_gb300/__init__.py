@@ -109,6 +109,8 @@ _sig = {
     "jb_state_bytes": (C.c_size_t, [_vp]),
     "jb_save_state": (C.c_int32, [_vp, _vp, C.c_size_t]),
     "jb_load_state": (C.c_int32, [_vp, _vp, C.c_size_t]),
+    "jb_step_noalloc": (C.c_int32, [C.c_int32, _ip, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                    C.POINTER(jb_solver_params), C.c_int32, _vp]),
     "jb_status_str": (C.c_char_p, [C.c_int32]),
     "jb_last_error": (C.c_char_p, []),
     "jb_version": (C.c_char_p, []),

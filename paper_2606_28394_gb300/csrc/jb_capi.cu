@@ -10,6 +10,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <vector>
 
@@ -25,6 +26,7 @@ __global__ void protocol_start_kernel(Dev D);
 __global__ void push_kernel(Dev D, int n, const int* ep, const int* blk, const int* axis, const float* force, const int* steps);
 __global__ void remove_kernel(Dev D, int n, const int* ep, const int* blk);
 __global__ void stats_kernel(Dev D, jb_episode_stats* out);
+__global__ void pair_offsets_kernel(Dev D, int64_t* pair_off);
 }  // namespace jbk
 
 using namespace jbk;
@@ -617,6 +619,99 @@ jb_status jb_load_state(jb_batch* b, const void* host, size_t bytes) {
   CU(cudaMemcpyAsync(b->ws, host, b->persist_bytes, cudaMemcpyHostToDevice, b->stream));
   CU(cudaStreamSynchronize(b->stream));
   b->has_protocol = true;
+  return JB_OK;
+}
+
+
+// ------------------------------------------------- no-allocation stepping
+// Scratch for jb_step_noalloc: a fixed device array that lives as long as the
+// library is loaded on a device.  Host code must not use the symbol as an
+// address; it asks the runtime for the device address once per device.
+static __device__ __align__(256) unsigned char jb_static_scratch[JB_NOALLOC_SCRATCH_BYTES];
+
+static std::mutex g_scratch_mutex;
+static void* g_scratch_addr[256];
+
+// Device address of jb_static_scratch on the current device (looked up on the
+// first call per device).
+static jb_status static_scratch_address(void** out) {
+  int dev = 0;
+  CU(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) return fail(JB_ECUDA, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t err = cudaGetSymbolAddress(&p, jb_static_scratch);
+    if (err != cudaSuccess || !p)
+      return fail(JB_ECUDA, "cudaGetSymbolAddress(jb_static_scratch) failed: %s", cudaGetErrorString(err));
+    g_scratch_addr[dev] = p;
+  }
+  *out = g_scratch_addr[dev];
+  return JB_OK;
+}
+
+jb_status jb_step_noalloc(int32_t n_episodes, const int32_t* body_off, const float* d_half, const float* d_mass,
+                          const float* d_mu, const float* d_ground_mu, float* d_x, float* d_q, float* d_v,
+                          float* d_w, const jb_solver_params* p, int32_t n_steps, void* cuda_stream) {
+  if (!body_off || !d_half || !d_mass || !d_mu || !d_ground_mu || !d_x || !d_q || !d_v || !d_w || !p)
+    return fail(JB_EINVAL, "jb_step_noalloc: null argument");
+  if (n_steps < 0) return fail(JB_EINVAL, "jb_step_noalloc: n_steps must be >= 0");
+  if (const char* m = check_params(p)) return fail(JB_EINVAL, "jb_step_noalloc: %s", m);
+  Sizes z;
+  if (!sizes_of(n_episodes, body_off, 0, z, nullptr))
+    return fail(JB_EINVAL, "jb_step_noalloc: bad n_episodes/body_off");
+  for (int e = 0; e < z.E; ++e)
+    if (body_off[e + 1] < body_off[e]) return fail(JB_EINVAL, "jb_step_noalloc: body_off must be non-decreasing");
+  Dev D;
+  memset(&D, 0, sizeof D);
+  const size_t need = carve(nullptr, z, D, nullptr, nullptr, nullptr);
+  if (need > (size_t)JB_NOALLOC_SCRATCH_BYTES)
+    return fail(JB_ENOMEM, "jb_step_noalloc: this batch needs %zu bytes of scratch, the static scratch holds %u",
+                need, (unsigned)JB_NOALLOC_SCRATCH_BYTES);
+  if (n_steps == 0) return JB_OK;
+  void* base = nullptr;
+  if (jb_status st = static_scratch_address(&base)) return st;
+  carve(static_cast<unsigned char*>(base), z, D, nullptr, nullptr, nullptr);
+  D.E = z.E; D.B = z.B; D.nb_max = z.nb_max; D.pc_max = z.pc_max;
+  D.P = to_params(p);
+  D.ps = smem_pairs(z.nb_max, z.pc_max);
+  D.smem_per_warp = smem_plan(z.nb_max, z.pc_max, D.ps).bytes;
+  D.order = nullptr;   // episodes in index order
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  int dev = 0, nsm = 0, occ = 0, smem_max = 0;
+  const int smem = kWarpsPerCta * D.smem_per_warp;
+  CU(cudaGetDevice(&dev));
+  CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  CU(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (smem > smem_max) return fail(JB_EINVAL, "towers too large for shared memory (%d > %d bytes)", smem, smem_max);
+  CU(cudaFuncSetAttribute(episode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, episode_kernel, kWarpsPerCta * 32, smem));
+  if (occ < 1) return fail(JB_EINVAL, "episode kernel cannot be resident with %d bytes of shared memory", smem);
+  const unsigned grid = (unsigned)std::max(1, std::min((int)grid_of(z.E, kWarpsPerCta), occ * nsm));
+  const size_t fb = sizeof(float);
+  // inputs into the scratch copy of the batch layout; everything that must
+  // start at zero is written by the init kernels (the array keeps the last
+  // call's contents)
+  CU(cudaMemcpyAsync((void*)D.body_off, body_off, sizeof(int32_t) * (z.E + 1), cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(D.half, d_half, 3 * fb * z.B, cudaMemcpyDeviceToDevice, s));
+  CU(cudaMemcpyAsync(D.mass, d_mass, fb * z.B, cudaMemcpyDeviceToDevice, s));
+  CU(cudaMemcpyAsync(D.mu, d_mu, fb * z.B, cudaMemcpyDeviceToDevice, s));
+  CU(cudaMemcpyAsync((void*)D.ground_mu, d_ground_mu, fb * z.E, cudaMemcpyDeviceToDevice, s));
+  CU(cudaMemcpyAsync(D.x, d_x, 3 * fb * z.B, cudaMemcpyDeviceToDevice, s));
+  CU(cudaMemcpyAsync(D.q, d_q, 4 * fb * z.B, cudaMemcpyDeviceToDevice, s));
+  CU(cudaMemcpyAsync(D.v, d_v, 3 * fb * z.B, cudaMemcpyDeviceToDevice, s));
+  CU(cudaMemcpyAsync(D.w, d_w, 3 * fb * z.B, cudaMemcpyDeviceToDevice, s));
+  CU(cudaMemsetAsync(D.mv_off, 0, sizeof(int32_t) * (z.E + 1), s));
+  pair_offsets_kernel<<<1, 1, 0, s>>>(D, const_cast<int64_t*>(D.pair_off));
+  if (z.B > 0) init_bodies_kernel<<<grid_of(z.B, 256), 256, 0, s>>>(D);
+  init_episodes_kernel<<<grid_of(z.E, 256), 256, 0, s>>>(D);
+  CU(cudaMemsetAsync(D.work_counter, 0, sizeof(int32_t), s));
+  episode_kernel<<<grid, kWarpsPerCta * 32, smem, s>>>(D, kModeFree, n_steps);
+  CU(cudaGetLastError());
+  CU(cudaMemcpyAsync(d_x, D.x, 3 * fb * z.B, cudaMemcpyDeviceToDevice, s));
+  CU(cudaMemcpyAsync(d_q, D.q, 4 * fb * z.B, cudaMemcpyDeviceToDevice, s));
+  CU(cudaMemcpyAsync(d_v, D.v, 3 * fb * z.B, cudaMemcpyDeviceToDevice, s));
+  CU(cudaMemcpyAsync(d_w, D.w, 3 * fb * z.B, cudaMemcpyDeviceToDevice, s));
   return JB_OK;
 }
 

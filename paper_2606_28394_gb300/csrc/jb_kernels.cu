@@ -1342,6 +1342,18 @@ __global__ void reset_reference_kernel(Dev D) {
   D.z0[2 * D.B + b] = 1.f - 2.f * (q1 * q1 + q2 * q2);
 }
 
+// Pair-capacity prefix over the episodes (one thread; used where the host
+// keeps no offset table).
+__global__ void pair_offsets_kernel(Dev D, int64_t* pair_off) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  int64_t acc = 0;
+  pair_off[0] = 0;
+  for (int e = 0; e < D.E; ++e) {
+    acc += pair_capacity(D.body_off[e + 1] - D.body_off[e]);
+    pair_off[e + 1] = acc;
+  }
+}
+
 __global__ void clear_cache_kernel(Dev D) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= D.E) return;
