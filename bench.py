@@ -80,6 +80,19 @@ def workload(args, rank):
     return scene, prot, prm
 
 
+def reduce_ranks(times_ms, walls_s, body_steps, device, dist=None):
+    """Whole-job aggregation over ranks: the slowest rank's device time and
+    host time (MAX) against the body-steps of all ranks (SUM).  Ranks share
+    no data on the step itself; only these totals cross ranks."""
+    import torch
+    t = torch.tensor([float(times_ms), float(walls_s)], device=device, dtype=torch.float64)
+    tot = torch.tensor([float(body_steps)], device=device, dtype=torch.float64)
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+    return float(t[0].item()), float(t[1].item()), float(tot[0].item())
+
+
 def algorithmic_flops(st):
     return (FLOP_POINT_SWEEP * st["point_sweeps"].sum() + FLOP_POINT_SETUP * st["point_steps"].sum()
             + FLOP_PAIR * st["pair_steps"].sum() + FLOP_BP * st["bp_tests"].sum()
@@ -248,16 +261,12 @@ def main():
     ms = float(sum(times))
     body_steps = float(st["body_steps"].sum())
     flops = algorithmic_flops(st)
-    t = torch.tensor([ms, sum(walls)], device=dev, dtype=torch.float64)
-    tot = torch.tensor([body_steps * args.steps], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
-    ms_max, wall_max = float(t[0].item()), float(t[1].item())
-    value = float(tot.item()) / (ms_max / 1e3)
+    ms_max, wall_max, total_body_steps = reduce_ranks(ms, sum(walls), body_steps * args.steps, dev,
+                                                       dist if world > 1 else None)
+    value = total_body_steps / (ms_max / 1e3)
     e2e = None
     if not args.no_e2e:
-        e2e = {"value": float(tot.item()) / wall_max, "unit": "body-steps/s",
+        e2e = {"value": total_body_steps / wall_max, "unit": "body-steps/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "gpu_launches_per_step": 5,
                "note": "host wall clock over jb_batch_create (scene upload from pageable host arrays), "
