@@ -29,7 +29,7 @@
 #endif
 
 #define MAXP 4          /* contact points per pair (Sec. 6.2.1 step d) */
-#define TIE_ABS 1e-7    /* reading: SAT axis hysteresis (m) */
+#define TIE_ABS 1e-5    /* reading: SAT axis hysteresis (m), far below the 0.4 mm slop */
 #define EDGE_REL 0.05   /* reading: cross axis must beat the face axis by 5% */
 #define CROSS_EPS 1e-6  /* reading: skip degenerate cross axes */
 #define INC_TIE 1e-9    /* reading: incident-face choice hysteresis */
@@ -170,8 +170,12 @@ static void sat15(const box_t* A, const box_t* B, double delta[15], int valid[15
 
 /* Axis choice.  Reading (the paper only says "the axis with minimum delta"):
    face axes in order A0..B2, a later one replaces the current best only if
-   smaller by 1e-7 m; likewise among cross axes; a cross axis wins only if
-   delta_edge < delta_face - (0.05 |delta_face| + 1e-7).  Contact exists iff the
+   smaller by TIE_ABS; likewise among cross axes; a cross axis wins only if
+   delta_edge < delta_face - (0.05 |delta_face| + TIE_ABS).  The hysteresis
+   keeps nearly parallel choices stable: stacked blocks have A's and B's face
+   normals and the crossed-edge axis all near z, and a smaller tolerance lets
+   micro-radian tilts flip the pair between them (and between 4-point face
+   and 1-point edge manifolds) from step to step.  Contact exists iff the
    minimum delta over all valid axes exceeds -margin (speculative contacts). */
 static int sat_select(const double delta[15], const int valid[15], double* dmin_out) {
   double dmin = delta[0];

@@ -110,7 +110,7 @@ struct Contact {
   float depth[kMaxPts];
 };
 
-constexpr float kTieAbs = 1e-7f;    // SAT axis hysteresis (m)
+constexpr float kTieAbs = 1e-5f;    // SAT axis hysteresis (m): keeps near-parallel axis choices stable
 constexpr float kEdgeRel = 0.05f;   // a cross axis must beat the best face axis by 5 %
 constexpr float kCrossEps = 1e-6f;  // degenerate cross axes are skipped
 constexpr float kIncTie = 1e-9f;
