@@ -83,6 +83,9 @@ def lib():
         L.or_ground_manifold.argtypes = [dp, dp, dp, C.c_double, dp]
         L.or_rotmat.argtypes = [dp, dp]
         L.or_body_inertia.argtypes = [C.c_double, dp, dp]
+        L.or_set_recorder.argtypes = [vp, dp, C.c_int, C.c_int]
+        L.or_recorded.argtypes = [vp]
+        L.or_recorded.restype = C.c_long
         L.or_support_margin.argtypes = [C.c_int, dp, dp]
         L.or_support_margin.restype = C.c_double
         _lib = L
@@ -158,6 +161,16 @@ class World:
     def set_state(self, x, q, v, w):
         arrs = [_d(a) for a in (x, q, v, w)]
         lib().or_set_state(self.h, *[a[1] for a in arrs])
+
+    def set_recorder(self, capacity, every=1):
+        """Record (features, converged impulses) rows; returns the buffer."""
+        self._rec = np.zeros((max(capacity, 1), 27))
+        lib().or_set_recorder(self.h, self._rec.ctypes.data_as(C.POINTER(C.c_double)), int(capacity), int(every))
+        return self._rec
+
+    def recorded(self):
+        n = lib().or_recorded(self.h)
+        return self._rec[:min(n, len(self._rec))]
 
     def clear_cache(self):
         lib().or_clear_cache(self.h)

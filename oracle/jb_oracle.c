@@ -60,6 +60,8 @@ typedef struct {
   double k[MAXP][3];            /* inverse effective mass of rows n, t1, t2 */
   double bias[MAXP];
   double lam[MAXP][3];
+  int matched[MAXP];
+  double feat[MAXP][OR_NFEAT];
 } or_pair;
 
 typedef struct {
@@ -84,6 +86,10 @@ struct or_world {
   int* body_off;
   or_episode* ep;
   or_params P;
+  /* training-sample recorder */
+  double* rec;
+  int rec_cap, rec_every;
+  long rec_count;
   /* schedule storage */
   int *m_block, *m_axis, *m_remove, *m_push, *m_settle;
   double *m_sign, *m_factor, *m_k;
@@ -532,6 +538,7 @@ static void setup(or_episode* E, double h) {
       /* reading: separated points (depth < 0) may close the gap within the step */
       pr->bias[i] = pr->depth[i] < 0 ? -pr->depth[i] / h : 0.0;
       pr->lam[i][0] = pr->lam[i][1] = pr->lam[i][2] = 0;
+      pr->matched[i] = 0;
     }
   }
 }
@@ -567,7 +574,7 @@ static void warm_start_match(or_episode* E, const or_params* P) {
         double s = dot3(d, d);
         if (s <= bd) { bd = s; best = j; }
       }
-      if (best >= 0) memcpy(pr->lam[i], op->lam[best], sizeof(double) * 3);
+      if (best >= 0) { memcpy(pr->lam[i], op->lam[best], sizeof(double) * 3); pr->matched[i] = 1; }
     }
   }
 }
@@ -732,9 +739,61 @@ static void save_cache(or_episode* E) {
   E->nprev = E->np;
 }
 
+/* Warm-start network inputs of every point (learned warm start, not in the
+   paper): pre-solve relative point velocity of B w.r.t. A along n, t1, t2
+   over |g| h; depth over the margin; n; t1; m_bar/m of A and B (0 if
+   static); body inertia diagonals over m_bar L_bar^2 (0 if static); mu;
+   matched previous-frame impulses over m_bar |g| h; matched flag; ground flag. */
+#define FEAT_MASS 0.015
+#define FEAT_LEN 0.075
+static void features(or_episode* E, const or_params* P, double h) {
+  double gh = norm3(P->gravity) * h;
+  double sI = 1.0 / (FEAT_MASS * FEAT_LEN * FEAT_LEN);
+  for (int c = 0; c < E->np; ++c) {
+    or_pair* pr = &E->pairs[c];
+    or_body *A = body_ref(E, pr->a), *B = body_ref(E, pr->b);
+    double IA[3] = {0, 0, 0}, IB[3] = {0, 0, 0};
+    if (pr->a >= 0 && !A->is_static) { or_body_inertia(A->mass, A->half, IA); for (int k = 0; k < 3; ++k) IA[k] *= sI; }
+    if (!B->is_static) { or_body_inertia(B->mass, B->half, IB); for (int k = 0; k < 3; ++k) IB[k] *= sI; }
+    for (int i = 0; i < pr->np; ++i) {
+      double wa[3], wb[3], u[3];
+      cross3(A->w, pr->rA[i], wa); cross3(B->w, pr->rB[i], wb);
+      for (int k = 0; k < 3; ++k) u[k] = (B->v[k] + wb[k]) - (A->v[k] + wa[k]);
+      double* f = pr->feat[i];
+      f[0] = dot3(u, pr->n) / gh; f[1] = dot3(u, pr->t1) / gh; f[2] = dot3(u, pr->t2) / gh;
+      f[3] = P->contact_margin > 0 ? pr->depth[i] / P->contact_margin : 0.0;
+      for (int k = 0; k < 3; ++k) { f[4 + k] = pr->n[k]; f[7 + k] = pr->t1[k]; }
+      f[10] = FEAT_MASS * A->invm; f[11] = FEAT_MASS * B->invm;
+      for (int k = 0; k < 3; ++k) { f[12 + k] = IA[k]; f[15 + k] = IB[k]; }
+      f[18] = pr->mu;
+      for (int k = 0; k < 3; ++k) f[19 + k] = pr->lam[i][k] / (FEAT_MASS * gh);
+      f[22] = pr->matched[i] ? 1.0 : 0.0;
+      f[23] = pr->a < 0 ? 1.0 : 0.0;
+    }
+  }
+}
+
+static void record(or_world* W, or_episode* E, const or_params* P, double h) {
+  double gh = norm3(P->gravity) * h;
+  for (int c = 0; c < E->np; ++c) {
+    or_pair* pr = &E->pairs[c];
+    for (int i = 0; i < pr->np; ++i) {
+      long slot;
+#ifdef _OPENMP
+#pragma omp atomic capture
+#endif
+      slot = W->rec_count++;
+      if (slot >= W->rec_cap) return;
+      double* row = W->rec + (size_t)slot * OR_REC;
+      memcpy(row, pr->feat[i], sizeof(double) * OR_NFEAT);
+      for (int k = 0; k < 3; ++k) row[OR_NFEAT + k] = pr->lam[i][k] / (FEAT_MASS * gh);
+    }
+  }
+}
+
 /* One substep of length h: forces, detection, setup, warm start, PGS,
    integration, position correction. */
-static void substep(or_episode* E, const or_params* P, double h) {
+static void substep(or_world* W, or_episode* E, const or_params* P, double h) {
   for (int i = 0; i < E->nb; ++i) {
     or_body* B = &E->b[i];
     if (!B->active || B->is_static) continue;
@@ -745,8 +804,11 @@ static void substep(or_episode* E, const or_params* P, double h) {
   detect(E, P);
   setup(E, h);
   warm_start_match(E, P);
+  const int rec = W && W->rec && ((E->solves % W->rec_every) == 0);
+  if (rec) features(E, P, h);
   apply_warm_start(E);
   solve(E, P);
+  if (rec && (P->residual_tol <= 0 || E->last_res <= P->residual_tol)) record(W, E, P, h);
   integrate(E, h);
   baumgarte(E, P);
   save_cache(E);
@@ -823,10 +885,10 @@ static void end_push(or_episode* E) {
 }
 
 /* One step (n_sub substeps) plus the episode schedule. */
-static void episode_step(or_episode* E, const or_params* P) {
+static void episode_step(or_world* W, or_episode* E, const or_params* P) {
   E->body_steps += count_dynamic(E);
   double h = P->dt / P->n_sub;
-  for (int s = 0; s < P->n_sub; ++s) substep(E, P, h);
+  for (int s = 0; s < P->n_sub; ++s) substep(W, E, P, h);
   for (int i = 0; i < E->nb; ++i)
     if (E->b[i].f_steps > 0) E->b[i].f_steps--;
   E->steps++;
@@ -977,7 +1039,7 @@ int or_run_protocol(or_world* W, int max_steps, int n_threads) {
   for (int e = 0; e < W->E; ++e) {
     or_episode* E = &W->ep[e];
     int s = 0;
-    while (s < max_steps && E->phase != OR_PH_DONE && E->phase != OR_PH_FREE) { episode_step(E, &W->P); ++s; }
+    while (s < max_steps && E->phase != OR_PH_DONE && E->phase != OR_PH_FREE) { episode_step(W, E, &W->P); ++s; }
     if (s > maxs) maxs = s;
   }
   (void)n_threads;
@@ -990,7 +1052,7 @@ void or_step(or_world* W, int n_steps, int n_threads) {
 #pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads)
 #endif
   for (int e = 0; e < W->E; ++e)
-    for (int s = 0; s < n_steps; ++s) episode_step(&W->ep[e], &W->P);
+    for (int s = 0; s < n_steps; ++s) episode_step(W, &W->ep[e], &W->P);
   (void)n_threads;
 }
 
@@ -1051,6 +1113,15 @@ void or_set_state(or_world* W, const double* x, const double* q, const double* v
       update_frame(B);
     }
 }
+
+void or_set_recorder(or_world* W, double* rows, int capacity, int every) {
+  W->rec = capacity > 0 ? rows : NULL;
+  W->rec_cap = capacity;
+  W->rec_every = every > 0 ? every : 1;
+  W->rec_count = 0;
+}
+
+long or_recorded(const or_world* W) { return W->rec_count; }
 
 void or_clear_cache(or_world* W) {
   for (int e = 0; e < W->E; ++e) W->ep[e].nprev = 0;

@@ -57,6 +57,9 @@ enum { OR_STATUS_NOT_CONVERGED = 2, OR_STATUS_NONFINITE = 4 };
    then 4 x { p[3], depth, lambda[3] (n, t1, t2), local_in_A[3] } */
 #define OR_CREC 55
 
+#define OR_NFEAT 24   /* warm-start features per contact point */
+#define OR_REC 27     /* recorder row: features, then converged impulses over m_bar |g| h */
+
 or_world* or_create(int n_episodes, const int* body_off, const double* half,
                     const double* mass, const double* mu, const double* x,
                     const double* q, const double* v, const double* w,
@@ -75,6 +78,11 @@ void or_get_state(const or_world* W, double* x, double* q, double* v, double* w)
 void or_set_state(or_world* W, const double* x, const double* q, const double* v,
                   const double* w);
 void or_clear_cache(or_world* W);
+/* Training-sample recorder: after every `every`-th converged solve (counted
+   per episode), each contact point appends one OR_REC row (caller buffer of
+   `capacity` rows; or_recorded returns rows claimed, may exceed capacity). */
+void or_set_recorder(or_world* W, double* rows, int capacity, int every);
+long or_recorded(const or_world* W);
 int or_get_contacts(const or_world* W, int episode, double* out, int cap);
 void or_get_stats(or_world* W, double* out);
 double or_com_imbalance(const or_world* W, int episode);

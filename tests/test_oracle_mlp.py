@@ -1,0 +1,94 @@
+"""Pins of the FP64 warm-start network and of the oracle's feature recorder
+(CPU only): finite differences, closed forms, the AdamW formulas, and hand
+values of the features of a block resting on the ground."""
+import math
+
+import numpy as np
+
+import oracle
+import synth
+from oracle import mlp
+
+
+def data(rng, n=37):
+    X = rng.normal(size=(n, mlp.N_IN))
+    T = rng.normal(size=(n, mlp.N_OUT))
+    return X, T
+
+
+def test_gradient_matches_central_differences():
+    rng = np.random.default_rng(3)
+    theta = mlp.init(1) * 0.7
+    theta += rng.normal(0, 0.05, theta.shape)     # nonzero biases
+    X, T = data(rng)
+    g, L = mlp.grad(theta, X, T)
+    assert abs(L - mlp.loss(theta, X, T)) < 1e-12
+    idx = rng.choice(mlp.N_PARAM, 300, replace=False)
+    h = 1e-6
+    for i in idx:
+        e = np.zeros_like(theta); e[i] = h
+        fd = (mlp.loss(theta + e, X, T) - mlp.loss(theta - e, X, T)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)) + 1e-9, (i, fd, g[i])
+
+
+def test_zero_weights_give_bias_and_its_gradient():
+    rng = np.random.default_rng(4)
+    p = mlp.unflatten(np.zeros(mlp.N_PARAM))
+    p["b3"] = np.array([0.3, -0.2, 1.1])
+    theta = mlp.flatten(p)
+    X, T = data(rng, 11)
+    Y, _ = mlp.forward(theta, X)
+    assert np.allclose(Y, p["b3"])
+    g = mlp.unflatten(mlp.grad(theta, X, T)[0])
+    assert np.allclose(g["b3"], 2 * (p["b3"] - T).mean(0))
+    # no gradient reaches the weights through dead (zero) ReLUs except W3's inputs, which are zero
+    assert np.abs(g["W3"]).max() == 0 and np.abs(g["W1"]).max() == 0
+
+
+def test_positive_region_is_the_linear_map():
+    rng = np.random.default_rng(5)
+    p = {"W1": rng.uniform(0.01, 0.1, (24, 128)), "b1": rng.uniform(0, 0.1, 128),
+         "W2": rng.uniform(0.01, 0.1, (128, 128)), "b2": rng.uniform(0, 0.1, 128),
+         "W3": rng.normal(size=(128, 3)), "b3": rng.normal(size=3)}
+    X = rng.uniform(0, 1, (9, 24))
+    Y, _ = mlp.forward(mlp.flatten(p), X)
+    lin = ((X @ p["W1"] + p["b1"]) @ p["W2"] + p["b2"]) @ p["W3"] + p["b3"]
+    assert np.allclose(Y, lin, rtol=1e-12, atol=1e-12)
+
+
+def test_adamw_first_step_formula():
+    rng = np.random.default_rng(6)
+    theta = rng.normal(size=mlp.N_PARAM)
+    g = rng.normal(size=mlp.N_PARAM)
+    lr, wd = 1e-3, 1e-2
+    new, m, v = mlp.adamw(theta, g, np.zeros_like(g), np.zeros_like(g), 1, lr, wd=wd, eps=0.0)
+    # first step: mhat = g, vhat = g^2 -> update -lr sign(g); decay on weights only
+    decay = np.where(mlp.is_bias_mask(), 0.0, wd)
+    assert np.allclose(new, theta * (1 - lr * decay) - lr * np.sign(g), rtol=0, atol=1e-15)
+
+
+def test_recorder_features_of_a_resting_block():
+    hx, hy, hz = 0.0375, 0.0125, 0.0075
+    m, mu = 0.015, 0.4
+    sc = synth.custom_scene([dict(half=(hx, hy, hz), x=(0, 0, hz), mass=m, mu=mu)], ground_mu=mu)
+    for k in ("half", "x", "q", "v", "w", "mass", "mu", "ground_mu"):
+        setattr(sc, k, getattr(sc, k).astype(float))
+    sc.half[:, 0] = (hx, hy, hz); sc.x[:, 0] = (0, 0, hz); sc.mass[:] = m
+    W = oracle.World(sc, synth.params(residual_tol=1e-10, pgs_iter_cap=20000))
+    W.set_recorder(64, 1)
+    W.step(2)
+    rows = W.recorded()
+    assert len(rows) == 8      # 4 ground points, two steps
+    I = oracle.body_inertia(m, [hx, hy, hz]) / (0.015 * 0.075 ** 2)
+    gh = 9.81 / 240.0
+    for r in rows[:4]:        # first step: nothing to match yet
+        assert np.allclose(r[0:3], [-1, 0, 0], atol=1e-12)        # u = -g h along n
+        assert abs(r[3]) < 1e-9                                   # touching
+        assert np.allclose(r[4:10], [0, 0, 1, 1, 0, 0])
+        assert r[10] == 0 and abs(r[11] - 0.015 / m) < 1e-12
+        assert np.allclose(r[12:15], 0) and np.allclose(r[15:18], I)
+        assert abs(r[18] - mu) < 1e-7 and np.allclose(r[19:23], 0) and r[23] == 1
+    assert abs(rows[:4, 24].sum() - m / 0.015) < 1e-9               # total normal impulse m g h
+    for r, prev in zip(rows[4:], rows[:4]):   # second step: matched, previous impulses
+        assert r[22] == 1
+    assert abs(rows[4:, 19].sum() - m / 0.015) < 1e-9
