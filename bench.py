@@ -62,6 +62,12 @@ def parse():
                     help="fixed-sweep mode with this many sweeps per solve (profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--warm-start", default="learned", choices=["learned", "plain"],
+                    help="learned: train the warm-start network first and keep it if the gate passes")
+    ap.add_argument("--train-episodes", type=int, default=96)
+    ap.add_argument("--train-steps", type=int, default=480)
+    ap.add_argument("--train-rows", type=int, default=3_000_000)
+    ap.add_argument("--gate-episodes", type=int, default=48)
     ap.add_argument("--cpu-episodes", type=int, default=0)
     ap.add_argument("--cpu-steps", type=int, default=30)
     return ap.parse_args()
@@ -91,6 +97,36 @@ def reduce_ranks(times_ms, walls_s, body_steps, device, dist=None):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dist.all_reduce(tot, op=dist.ReduceOp.SUM)
     return float(t[0].item()), float(t[1].item()), float(tot[0].item())
+
+
+MLP_FLOP = 2.0 * (24 * 128 + 128 * 128 + 128 * 3)   # per predicted contact point
+
+
+def prepare_learned(args, rank, prm, device):
+    """Trains the warm-start network and gates it (plain PGS is the judge).
+    Samples: the plain solver's converged impulses on removal-round towers with
+    other seeds than the benchmark (training 3001 + rank, gate 4001 + rank)."""
+    from paper_2606_28394_gb300 import warmstart as ws
+    import torch
+    t0 = time.perf_counter()
+    sc, pr, _ = synth.friction_workload(seed=3001 + rank)
+    s_tr, p_tr = synth.subset(sc, pr, np.linspace(0, sc.n_episodes - 1, args.train_episodes).round().astype(int))
+    rows = ws.collect(s_tr, p_tr, prm, capacity=args.train_rows, every=2, max_steps=args.train_steps, device=device)
+    t1 = time.perf_counter()
+    net, hist = ws.train(rows, epochs=30, batch=8192, lr=3e-4, wd=1e-4, device=device)
+    torch.cuda.synchronize(device)
+    t2 = time.perf_counter()
+    sc2, pr2, _ = synth.friction_workload(seed=4001 + rank)
+    s_ev, p_ev = synth.subset(sc2, pr2, np.linspace(0, sc2.n_episodes - 1, args.gate_episodes).round().astype(int))
+    gate = ws.evaluate(s_ev, p_ev, prm, net, mode=2, max_steps=args.train_steps, device=device)
+    t3 = time.perf_counter()
+    info = {"samples": int(rows.shape[0]), "collect_s": t1 - t0, "train_s": t2 - t1, "gate_s": t3 - t2,
+            "epochs": 30, "final_train_loss": hist[-1][1], "final_val_loss": hist[-1][2],
+            "gate": {"episodes": args.gate_episodes, "steps": args.train_steps,
+                     "plain_sweeps_per_solve": gate["plain"]["sweeps_per_solve"],
+                     "learned_sweeps_per_solve": gate["learned"]["sweeps_per_solve"],
+                     "gain": gate["gain"]}, "kept": bool(gate["keep"])}
+    return net, info
 
 
 def algorithmic_flops(st):
@@ -184,7 +220,7 @@ def run_reference(args):
         if i >= args.warmup:
             vals.append(cb)
     v = statistics.mean(c["value"] for c in vals)
-    line = {"impl": "reference", "metric": "body-steps/s at PGS residual <= 1e-5 (plain PGS)",
+    line = {"impl": "reference", "metric": "body-steps/s at PGS residual <= 1e-5: learned warm start vs plain PGS",
             "value": v, "unit": "body-steps/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(c["seconds"] for c in vals),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -227,18 +263,26 @@ def main():
                                                     "remove", "push_steps", "settle_steps")))
     d2h = scene.n_episodes * jb.C.sizeof(jb.jb_episode_stats)
 
-    def job(max_steps):
+    net, learned = None, None
+    if args.warm_start == "learned":
+        net, learned = prepare_learned(args, rank, prm, dev)
+    run_prm = dict(prm, warm_start=2 if (learned and learned["kept"]) else 1)
+
+    def job(max_steps, params=None):
         """One pass through the C ABI from host buffers: create the batch
         (scene upload), upload the schedule, run every episode through it in
         one persistent launch, read the statistics back.  CUDA events bracket
         the launch (inputs resident); the host clock brackets the whole pass."""
+        params = params or run_prm
         flush.fill_(1)
         torch.cuda.synchronize(dev)
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         t0 = time.perf_counter()
-        b = jb.Batch(scene, prm, max_moves=M, stream=stream, device=dev, workspace=ws)
+        b = jb.Batch(scene, params, max_moves=M, stream=stream, device=dev, workspace=ws)
+        if params["warm_start"] >= 2:
+            jb.check(jb.jb_set_warmstart_mlp(b.h, net.block.data_ptr()), "jb_set_warmstart_mlp")
         b.set_protocol(prot)
         e0.record(stream)
         b.run_protocol(max_steps)
@@ -261,6 +305,14 @@ def main():
     ms = float(sum(times))
     body_steps = float(st["body_steps"].sum())
     flops = algorithmic_flops(st)
+    mlp_flops = MLP_FLOP * float(st["mlp_points"].sum())
+    plain = None
+    if run_prm["warm_start"] >= 2:
+        # the judge: the same job with plain PGS (previous-frame warm start)
+        ms_p, _, st_p = job(args.max_steps, dict(prm, warm_start=1))
+        ms_pm, _, bs_p = reduce_ranks(ms_p, 0.0, float(st_p["body_steps"].sum()), dev, dist if world > 1 else None)
+        plain = {"value": bs_p / (ms_pm / 1e3), "ms_per_step": ms_pm,
+                 "sweeps_per_solve": float(st_p["total_sweeps"].sum() / max(st_p["solves"].sum(), 1))}
     ms_max, wall_max, total_body_steps = reduce_ranks(ms, sum(walls), body_steps * args.steps, dev,
                                                        dist if world > 1 else None)
     value = total_body_steps / (ms_max / 1e3)
@@ -278,10 +330,12 @@ def main():
     achieved = flops / (ms / args.steps / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
             "frac": achieved / peak_tf, "traffic": None,
+            "mlp_flops_per_launch": mlp_flops,
+            "mlp_roofline_ms": mlp_flops / (float(peaks.get("bf16_tflops", 1892.9)) * 1e12) * 1e3,
             "peak_note": f"FP32 FMA peak: {SMS} SMs x {FP32_LANES} lanes x 2 flop x {sm_max:.0f} MHz (max SM clock of measured)",
             "kernel": "episode_kernel (persistent, one warp per episode)",
             "flops_per_launch": flops}
-    line = {"metric": "body-steps/s at PGS residual <= 1e-5 (plain PGS, previous-frame warm start)",
+    line = {"metric": "body-steps/s at PGS residual <= 1e-5: learned warm start vs plain PGS",
             "value": value, "unit": "body-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -292,6 +346,10 @@ def main():
                        "l2": "flushed (256 MB write) before every timed step",
                        "warmup": f"{args.warmup} passes of the job truncated to {args.warmup_steps} physics steps",
                        "episodes": scene.n_episodes, "bodies": scene.n_bodies},
+            "warm_start": {"mode": "learned (network on unmatched points, previous-frame elsewhere)"
+                           if run_prm["warm_start"] >= 2 else "plain (previous-frame)",
+                           "training": learned, "plain_judge": plain,
+                           "learned_over_plain": (value / plain["value"]) if plain else None},
             "roofline": roof, "gpu_launches": args.steps, "clocks": clk.summary(),
             "e2e": e2e,
             "solver": {"sweeps_per_solve": float(st["total_sweeps"].sum() / max(st["solves"].sum(), 1)),

@@ -86,7 +86,9 @@ typedef struct {
   float contact_margin;     /* speculative contact margin m_c, m */
   float aabb_eps;           /* Eq. aabb epsilon, m */
   float gravity[3];         /* m/s^2 */
-  int32_t warm_start;       /* 0 none, 1 previous-frame impulses */
+  int32_t warm_start;       /* 0 none, 1 previous-frame impulses, 2 previous-frame where a
+                               point matches and the warm-start network elsewhere, 3 the
+                               network for every point (2 and 3 need jb_set_warmstart_mlp) */
   float match_radius;       /* warm-start point match radius, m */
   float fall_frac;          /* Eq. collapse f_d */
   float collapse_ek;        /* Eq. collapse eps_k, J */
@@ -174,6 +176,7 @@ typedef struct {
   /* work counters (sums over substeps): contact points x sweeps, contact
      points, contact pairs, broadphase pair tests */
   double point_sweeps, point_steps, pair_steps, bp_tests;
+  double mlp_points;        /* contact points whose start came from the warm-start network */
 } jb_episode_stats;
 
 typedef struct jb_batch jb_batch;
@@ -249,6 +252,63 @@ jb_status jb_read_episode_stats(jb_batch* b, jb_episode_stats* out);
 size_t jb_state_bytes(const jb_batch* b);
 jb_status jb_save_state(jb_batch* b, void* host_buf, size_t bytes);
 jb_status jb_load_state(jb_batch* b, const void* host_buf, size_t bytes);
+
+/* ---- Learned warm start (not in the paper: a small network that predicts
+ * a contact point's starting impulses from local features; plain PGS stays
+ * the judge of convergence).
+ *
+ * Features (JB_FEATURES floats per contact point, computed after the force
+ * predictor and before the solve, with s_v = 1/(|g| h), s_l = 1/(m_bar |g| h),
+ * m_bar = 0.015 kg, L_bar = 0.075 m, h the substep):
+ *   0-2   relative point velocity of b w.r.t. a along n, t1, t2, times s_v
+ *   3     depth / contact_margin
+ *   4-9   n, t1
+ *   10-11 m_bar / m of a, b (0 for static bodies and the ground)
+ *   12-17 body-frame inertia diagonals of a, b over m_bar L_bar^2 (0 if static)
+ *   18    friction coefficient
+ *   19-21 previous-frame impulses (n, t1, t2) times s_l (0 if unmatched)
+ *   22    1 if the point matched a previous-frame point
+ *   23    1 if a is the ground
+ * Outputs: impulses (n, t1, t2) times s_l, projected to lambda_n >= 0 and
+ * |lambda_t| <= mu lambda_n before use.
+ * Network: 24 -> 128 -> 128 -> 3, ReLU, parameters W1 [24][128], b1, W2
+ * [128][128], b2, W3 [128][3], b3 (row-major [in][out], FP32 master copy,
+ * BF16 tensor-core operands with FP32 accumulation). */
+#define JB_FEATURES 24
+#define JB_REC_FLOATS 27   /* recorder row: features, then converged impulses times s_l */
+
+/* The batch uses the network block d_mlp (device, jb_mlp_bytes, caller
+ * owned; NULL removes it) for warm_start 2 and 3. */
+jb_status jb_set_warmstart_mlp(jb_batch* b, const void* d_mlp);
+/* Training-sample recorder: after every `every`-th converged solve, each
+ * contact point appends one JB_REC_FLOATS row to d_rows (device, capacity
+ * rows); *d_count (device int32, caller zeroes it) counts rows claimed and may
+ * exceed capacity (extra rows are dropped).  capacity 0 turns it off. */
+jb_status jb_set_recorder(jb_batch* b, float* d_rows, int32_t capacity, int32_t* d_count, int32_t every);
+
+size_t jb_mlp_bytes(void);              /* device bytes of a network block */
+int32_t jb_mlp_param_count(void);       /* floats of one parameter set */
+size_t jb_mlp_scratch_bytes(int32_t n); /* device scratch for n rows */
+/* Loads parameters (host, jb_mlp_param_count floats, layout above) into the
+ * block, zeroes the AdamW moments and packs the BF16 operands. */
+jb_status jb_mlp_load(void* d_mlp, const float* params, void* cuda_stream);
+jb_status jb_mlp_save(const void* d_mlp, float* params, void* cuda_stream);
+/* y [n][3] = network(x [n][24]); device arrays. */
+jb_status jb_mlp_forward(const void* d_mlp, const float* d_x, int32_t n, float* d_y, void* d_scratch,
+                         size_t scratch_bytes, void* cuda_stream);
+/* Gradient of L = (1/n) sum_rows sum_c (y - t)^2 with respect to the
+ * parameters (d_grad, FP32, parameter layout) and L itself (d_loss, may be
+ * NULL); t [n][3]. */
+jb_status jb_mlp_grad(const void* d_mlp, const float* d_x, const float* d_t, int32_t n, float* d_grad,
+                      float* d_loss, void* d_scratch, size_t scratch_bytes, void* cuda_stream);
+/* AdamW step `step` (1-based) on the master weights (weight decay on the
+ * matrices only), then repack. */
+jb_status jb_mlp_adamw(void* d_mlp, const float* d_grad, int32_t step, float lr, float beta1, float beta2,
+                       float eps, float weight_decay, void* cuda_stream);
+/* jb_mlp_grad on rows [0, n) of (x, t) followed by jb_mlp_adamw. */
+jb_status jb_mlp_train_step(void* d_mlp, const float* d_x, const float* d_t, int32_t n, int32_t step, float lr,
+                            float beta1, float beta2, float eps, float weight_decay, float* d_loss,
+                            void* d_scratch, size_t scratch_bytes, void* cuda_stream);
 
 /* Stepping for callers that cannot allocate device memory.
  *

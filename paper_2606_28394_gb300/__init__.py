@@ -81,7 +81,7 @@ class jb_episode_stats(C.Structure):
                 ("total_sweeps", C.c_double), ("solves", C.c_double),
                 ("body_steps", C.c_double), ("point_sweeps", C.c_double),
                 ("point_steps", C.c_double), ("pair_steps", C.c_double),
-                ("bp_tests", C.c_double)]
+                ("bp_tests", C.c_double), ("mlp_points", C.c_double)]
 
 
 _vp = C.c_void_p
@@ -109,6 +109,19 @@ _sig = {
     "jb_state_bytes": (C.c_size_t, [_vp]),
     "jb_save_state": (C.c_int32, [_vp, _vp, C.c_size_t]),
     "jb_load_state": (C.c_int32, [_vp, _vp, C.c_size_t]),
+    "jb_set_warmstart_mlp": (C.c_int32, [_vp, _vp]),
+    "jb_set_recorder": (C.c_int32, [_vp, _vp, C.c_int32, _vp, C.c_int32]),
+    "jb_mlp_bytes": (C.c_size_t, []),
+    "jb_mlp_param_count": (C.c_int32, []),
+    "jb_mlp_scratch_bytes": (C.c_size_t, [C.c_int32]),
+    "jb_mlp_load": (C.c_int32, [_vp, _fp, _vp]),
+    "jb_mlp_save": (C.c_int32, [_vp, _fp, _vp]),
+    "jb_mlp_forward": (C.c_int32, [_vp, _vp, C.c_int32, _vp, _vp, C.c_size_t, _vp]),
+    "jb_mlp_grad": (C.c_int32, [_vp, _vp, _vp, C.c_int32, _vp, _vp, _vp, C.c_size_t, _vp]),
+    "jb_mlp_adamw": (C.c_int32, [_vp, _vp, C.c_int32, C.c_float, C.c_float, C.c_float, C.c_float,
+                                 C.c_float, _vp]),
+    "jb_mlp_train_step": (C.c_int32, [_vp, _vp, _vp, C.c_int32, C.c_int32, C.c_float, C.c_float,
+                                      C.c_float, C.c_float, C.c_float, _vp, _vp, C.c_size_t, _vp]),
     "jb_step_noalloc": (C.c_int32, [C.c_int32, _ip, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                     C.POINTER(jb_solver_params), C.c_int32, _vp]),
     "jb_status_str": (C.c_char_p, [C.c_int32]),

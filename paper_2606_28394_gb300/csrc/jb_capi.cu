@@ -33,7 +33,7 @@ using namespace jbk;
 
 static thread_local char g_err[512] = "";
 
-static jb_status fail(jb_status s, const char* fmt, ...) {
+jb_status jbk::fail(jb_status s, const char* fmt, ...) {
   va_list ap;
   va_start(ap, fmt);
   vsnprintf(g_err, sizeof g_err, fmt, ap);
@@ -126,6 +126,7 @@ size_t carve(unsigned char* base, const Sizes& z, Dev& D, size_t* persist, int32
     c.srt_ab = a.take<uint32_t>(P);
     c.srt_np = a.take<int32_t>(P);
     c.srt_pt = a.take<float>((size_t)P * kPtStride);
+    c.nat_x = a.take<float>((size_t)P * kMaxPts * kFeatures);
   }
   if (persist) *persist = (a.off + 255) & ~size_t(255);
   D.work_counter = a.take<int32_t>(1);
@@ -190,7 +191,7 @@ const char* check_params(const jb_solver_params* p) {
   if (p->residual_every < 1) return "residual_every must be >= 1";
   if (!(p->contact_margin >= 0.f) || !(p->aabb_eps >= p->contact_margin))
     return "need 0 <= contact_margin <= aabb_eps";
-  if (p->warm_start < 0 || p->warm_start > 1) return "warm_start must be 0 or 1";
+  if (p->warm_start < 0 || p->warm_start > 3) return "warm_start must be 0, 1, 2 or 3";
   return nullptr;
 }
 
@@ -377,6 +378,23 @@ jb_status jb_batch_create(const jb_scene* sc, const jb_solver_params* p, int32_t
 
 void jb_batch_destroy(jb_batch* b) { delete b; }
 
+jb_status jb_set_warmstart_mlp(jb_batch* b, const void* d_mlp) {
+  if (!b) return fail(JB_EINVAL, "jb_set_warmstart_mlp: null batch");
+  b->D.mlp = static_cast<const unsigned char*>(d_mlp);
+  return JB_OK;
+}
+
+jb_status jb_set_recorder(jb_batch* b, float* d_rows, int32_t capacity, int32_t* d_count, int32_t every) {
+  if (!b) return fail(JB_EINVAL, "jb_set_recorder: null batch");
+  if (capacity < 0 || every < 0) return fail(JB_EINVAL, "jb_set_recorder: negative capacity or period");
+  if (capacity > 0 && (!d_rows || !d_count || every < 1)) return fail(JB_EINVAL, "jb_set_recorder: null buffer");
+  b->D.rec = capacity > 0 ? d_rows : nullptr;
+  b->D.rec_count = capacity > 0 ? d_count : nullptr;
+  b->D.rec_cap = capacity;
+  b->D.rec_every = every > 0 ? every : 1;
+  return JB_OK;
+}
+
 jb_status jb_set_params(jb_batch* b, const jb_solver_params* p) {
   if (!b || !p) return fail(JB_EINVAL, "jb_set_params: null argument");
   if (const char* m = check_params(p)) return fail(JB_EINVAL, "jb_set_params: %s", m);
@@ -426,6 +444,8 @@ jb_status jb_set_protocol(jb_batch* b, const jb_protocol* pr) {
 
 static jb_status launch_episodes(jb_batch* b, int mode, int n) {
   Dev& D = b->D;
+  if (D.P.warm_start >= 2 && !D.mlp)
+    return fail(JB_ESTATE, "learned warm start selected but no network set (jb_set_warmstart_mlp)");
   cudaStream_t s = b->stream;
   CU(cudaMemsetAsync(D.work_counter, 0, sizeof(int32_t), s));
   episode_kernel<<<b->grid, kWarpsPerCta * 32, kWarpsPerCta * D.smem_per_warp, s>>>(D, mode, n);

@@ -43,7 +43,7 @@ struct EpState {
   int32_t last_sweeps, steps, n_fallen, max_colours;
   float last_res, max_res, kinetic, com_imb;
   double total_sweeps, solves, body_steps;
-  double point_sweeps, point_steps, pair_steps, bp_tests;
+  double point_sweeps, point_steps, pair_steps, bp_tests, mlp_points;
 };
 
 struct Params {
@@ -74,7 +74,14 @@ struct ContactBuf {
   uint32_t* srt_ab;     // local a | local b << 16 (ground = nb)
   int32_t* srt_np;
   float* srt_pt;        // per episode: [Pc][kPtStride], point k field f at k * 13 + f
+  float* nat_x;         // [P * 4][kFeatures] warm-start features of each point
 };
+
+constexpr int kFeatures = 24;    // warm-start network inputs per contact point
+constexpr int kRecFloats = 27;   // recorder row: features, then converged impulses (n, t1, t2)
+// normalisation scales of the features (nominal block mass and length)
+constexpr float kFeatMass = 0.015f;
+constexpr float kFeatLen = 0.075f;
 
 struct Dev {
   int E, B, nb_max, pc_max;
@@ -94,7 +101,15 @@ struct Dev {
   Params P;
   int smem_per_warp;      // bytes
   int ps;                 // pairs whose solver arrays fit in shared memory
+  // warm-start network (caller-owned block) and training-sample recorder
+  const unsigned char* mlp;
+  float* rec;
+  int32_t* rec_count;
+  int rec_cap, rec_every;
 };
+
+// Error reporting shared by the library's translation units.
+jb_status fail(jb_status s, const char* fmt, ...);
 
 // Shared-memory plan of one episode (bytes from the warp's base).
 struct SmemPlan {

@@ -20,6 +20,7 @@
 #include <cstdint>
 
 #include "jb_internal.cuh"
+#include "jb_mlp.cuh"
 
 namespace jbk {
 
@@ -379,7 +380,7 @@ struct Ep {
 
 struct BufView {
   uint32_t *key, *feat, *slot;
-  float *pt, *pf;
+  float *pt, *pf, *x;
   // colour-sorted solver arrays: shared memory when the step's pairs fit,
   // else this buffer's global copy; field f of slot s at [f * stride + s]
   uint32_t* ab;
@@ -396,6 +397,7 @@ __device__ __forceinline__ BufView buf_view(const Dev& D, int which, const Ep& E
   v.slot = b.nat_slot + E.poff;
   v.pt = b.nat_pt + E.poff * kMaxPts * kNatPtFloats;
   v.pf = b.nat_pf + E.poff * kNatPairFloats;
+  v.x = b.nat_x + E.poff * kMaxPts * kFeatures;
   v.ab = b.srt_ab + E.poff;
   v.np = b.srt_np + E.poff;
   v.sf = b.srt_f + E.poff * kPairStride;
@@ -665,10 +667,95 @@ __device__ __forceinline__ float episode_residual(const SolverRef& r, int npairs
 
 #undef VF
 
+// ----------------------------------------------------- learned warm start
+// The warp collects the points to predict (ids p * 4 + k) into the
+// candidate array (free after the colouring), runs the network on tiles of 16
+// rows on the tensor cores and writes the projected impulses (lambda_n >= 0,
+// |lambda_t| <= mu lambda_n) as the points' starting impulses.
+__device__ __noinline__ int mlp_warm_start(const Dev& D, const Ep& E, const BufView& Bc, int npairs, bool all_points,
+                                           float imp_scale, int lane) {
+  const Sm& s = E.s;
+  const MlpLayout L = mlp_layout();
+  const float* P = reinterpret_cast<const float*>(D.mlp);
+  const uint2* pk = reinterpret_cast<const uint2*>(D.mlp + L.pack_base);
+  const int ccap = cand_capacity(E.nb);
+  uint32_t* list = s.cand;
+  float* stage = reinterpret_cast<float*>(s.cand + (ccap - 64));   // 16 rows x 4
+  const int lcap = ccap - 64;
+  const int g = lane >> 2, t = lane & 3;
+  int cnt = 0, predicted = 0;
+  for (int p0 = 0; p0 < npairs; p0 += 32) {
+    const int p = p0 + lane;
+    int mine = 0;
+    uint32_t ids[kMaxPts];
+    if (p < npairs) {
+      int np = Bc.feat[p] >> 24;
+      const float* pt = Bc.pt + (size_t)p * kMaxPts * kNatPtFloats;
+      for (int k = 0; k < np; ++k)
+        if (all_points || pt[k * kNatPtFloats + 10] == 0.f) ids[mine++] = (uint32_t)(p * kMaxPts + k);
+    }
+    int incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int v = __shfl_up_sync(FULL, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(FULL, incl, 31);
+    for (int i = 0; i < mine; ++i) list[cnt + incl - mine + i] = ids[i];
+    cnt += total;
+    predicted += total;
+    __syncwarp();
+    const bool last = p0 + 32 >= npairs;
+    if (!(last || cnt + 32 * kMaxPts > lcap)) continue;
+    // run the network over list[0, cnt)
+    for (int r0 = 0; r0 < cnt; r0 += 16) {
+      const int ia = r0 + g, ib = r0 + g + 8;
+      const float* xa = ia < cnt ? Bc.x + (size_t)list[ia] * kFeatures : nullptr;
+      const float* xb = ib < cnt ? Bc.x + (size_t)list[ib] * kFeatures : nullptr;
+      auto x = [&](const float* r, int c) { return (r && c < kFeatures) ? r[c] : 0.f; };
+      uint32_t a[2][4];
+#pragma unroll
+      for (int kk = 0; kk < 2; ++kk) {
+        int c = kk * 16 + 2 * t;
+        a[kk][0] = pack_bf16x2(x(xa, c), x(xa, c + 1));
+        a[kk][1] = pack_bf16x2(x(xb, c), x(xb, c + 1));
+        a[kk][2] = pack_bf16x2(x(xa, c + 8), x(xa, c + 9));
+        a[kk][3] = pack_bf16x2(x(xb, c + 8), x(xb, c + 9));
+      }
+      uint32_t h1[8][4], h2[8][4];
+      dense_relu_128<2>(a, pk + L.p1, P + L.b1, lane, h1);
+      dense_relu_128<8>(h1, pk + L.p2, P + L.b2, lane, h2);
+      float y[4];
+      dense_out(h2, pk + L.p3, P + L.b3, lane, y);
+      if (t < 2) {
+        stage[g * 4 + 2 * t] = y[0]; stage[g * 4 + 2 * t + 1] = y[1];
+        stage[(g + 8) * 4 + 2 * t] = y[2]; stage[(g + 8) * 4 + 2 * t + 1] = y[3];
+      }
+      __syncwarp();
+      if (lane < 16 && r0 + lane < cnt) {
+        uint32_t id = list[r0 + lane];
+        int p = id / kMaxPts, k = id % kMaxPts;
+        int sl = Bc.slot[p] & 0xffff;
+        float mu = Bc.sf[sl * kPairStride + 6];
+        float ln = fmaxf(0.f, stage[lane * 4 + 0] * imp_scale);
+        float lim = mu * ln;
+        float* rec = Bc.sp + sl * kPtStride + k * kSrtPtFloats;
+        rec[10] = ln;
+        rec[11] = fminf(fmaxf(stage[lane * 4 + 1] * imp_scale, -lim), lim);
+        rec[12] = fminf(fmaxf(stage[lane * 4 + 2] * imp_scale, -lim), lim);
+      }
+      __syncwarp();
+    }
+    cnt = 0;
+    __syncwarp();
+  }
+  return predicted;
+}
+
 // ------------------------------------------------------------------ substep
 struct StepOut {
   float res;
-  int sweeps;
+  int sweeps, predicted;
   int npairs, npoints, ncol;
   int status;
 };
@@ -817,7 +904,7 @@ __device__ StepOut substep(const Dev& D, const Ep& E, EpState& st, float h) {
       if (km == key) { q = mid; break; }
       if (km < key) lo = mid + 1; else hi = mid - 1;
     }
-    if (q < 0 || Pm.warm_start != 1) continue;
+    if (q < 0 || Pm.warm_start == 0) continue;
     uint32_t fn = Bc.feat[p], fo = Bp.feat[q];
     if (((fn ^ fo) & 0x00ffff00u) != 0) continue;
     int npn = fn >> 24, npo = fo >> 24;
@@ -836,6 +923,7 @@ __device__ StepOut substep(const Dev& D, const Ep& E, EpState& st, float h) {
       if (best >= 0) {   // the old point's final impulses of the previous step
         const float* o = pto + best * kNatPtFloats;
         a[7] = o[7]; a[8] = o[8]; a[9] = o[9];
+        a[10] = 1.f;     // matched
       }
     }
   }
@@ -936,6 +1024,13 @@ __device__ StepOut substep(const Dev& D, const Ep& E, EpState& st, float h) {
   // shared memory when the pairs fit, else this buffer's global copy
   if (npairs <= s.ps) use_smem_solver(Bc, s);
   const float ih = 1.f / h;
+  const bool want_features = (Pm.warm_start >= 2 && D.mlp) || D.rec != nullptr;
+  const float gmag = sqrtf(Pm.g[0] * Pm.g[0] + Pm.g[1] * Pm.g[1] + Pm.g[2] * Pm.g[2]);
+  const float gh = fmaxf(gmag * h, 1e-12f);
+  const float inv_gh = 1.f / gh;
+  const float imp_scale = kFeatMass * gh;   // impulse unit m_bar g h
+  const float inv_imp = 1.f / imp_scale;
+  const float inv_mc = Pm.contact_margin > 0.f ? 1.f / Pm.contact_margin : 0.f;
   for (int p = lane; p < npairs; p += 32) {
     uint32_t key = Bc.key[p];
     int a = (int)(key >> 16) - 1, b = (int)(key & 0xffff);
@@ -962,6 +1057,18 @@ __device__ StepOut substep(const Dev& D, const Ep& E, EpState& st, float h) {
     float3 xa = s.ld3(FX, ia), xb = s.ld3(FX, b);
     float ima = s.at(FM, ia), imb = s.at(FM, b);
     const Sym3 Ia = ld_iw(s, ia), Ib = ld_iw(s, b);
+    float3 Ibody_a = f3(0.f, 0.f, 0.f), Ibody_b = f3(0.f, 0.f, 0.f);
+    if (want_features) {
+      const float sI = 1.f / (kFeatMass * kFeatLen * kFeatLen);
+      if (a >= 0 && !(s.flags[a] & kStatic)) {
+        int ga = E.b0 + a;
+        Ibody_a = f3(sI / D.invI[ga], sI / D.invI[D.B + ga], sI / D.invI[2 * D.B + ga]);
+      }
+      if (!(s.flags[b] & kStatic)) {
+        int gb = E.b0 + b;
+        Ibody_b = f3(sI / D.invI[gb], sI / D.invI[D.B + gb], sI / D.invI[2 * D.B + gb]);
+      }
+    }
     for (int k = 0; k < np; ++k) {
       const float* q = pt + k * kNatPtFloats;
       float3 pp = f3(q[0], q[1], q[2]);
@@ -987,14 +1094,35 @@ __device__ StepOut substep(const Dev& D, const Ep& E, EpState& st, float h) {
       W(6, w01); W(7, w02); W(8, w12); W(9, bias);
       W(10, q[7]); W(11, q[8]); W(12, q[9]);
 #undef W
+      if (want_features) {
+        // warm-start features: pre-solve relative velocity in the contact
+        // frame, depth, frame, inverse masses, body inertias, mu, previous
+        // impulses and two flags, normalised by the nominal block
+        const float3 u = (s.ld3(FV, b) + cross(s.ld3(FW, b), rB)) - (s.ld3(FV, ia) + cross(s.ld3(FW, ia), rA));
+        float* f = Bc.x + ((size_t)p * kMaxPts + k) * kFeatures;
+        f[0] = dot(u, n) * inv_gh; f[1] = dot(u, t1) * inv_gh; f[2] = dot(u, t2) * inv_gh;
+        f[3] = dep * inv_mc;
+        f[4] = n.x; f[5] = n.y; f[6] = n.z; f[7] = t1.x; f[8] = t1.y; f[9] = t1.z;
+        f[10] = kFeatMass * ima; f[11] = kFeatMass * imb;
+        f[12] = Ibody_a.x; f[13] = Ibody_a.y; f[14] = Ibody_a.z;
+        f[15] = Ibody_b.x; f[16] = Ibody_b.y; f[17] = Ibody_b.z;
+        f[18] = mu;
+        f[19] = q[7] * inv_imp; f[20] = q[8] * inv_imp; f[21] = q[9] * inv_imp;
+        f[22] = q[10]; f[23] = a < 0 ? 1.f : 0.f;
+      }
     }
   }
   __syncwarp();
 
+  // (7b) learned warm start: the network predicts the starting impulses of the
+  // unmatched points (mode 2) or of all points (mode 3)
+  int predicted = 0;
+  if (Pm.warm_start >= 2 && D.mlp) predicted = mlp_warm_start(D, E, Bc, npairs, Pm.warm_start == 3, imp_scale, lane);
+
   // (8) warm start: apply the inherited impulses
   const SolverRef V = solver_ref(s, Bc);
   const float e1 = 1.f + Pm.restitution;
-  if (Pm.warm_start == 1) colour_passes<0>(V, s.off, ncol, lane, e1, Pm.beta, Pm.slop);
+  if (Pm.warm_start >= 1) colour_passes<0>(V, s.off, ncol, lane, e1, Pm.beta, Pm.slop);
 
   // (9) projected Gauss-Seidel sweeps
   int sweeps = 0;
@@ -1026,6 +1154,23 @@ __device__ StepOut substep(const Dev& D, const Ep& E, EpState& st, float h) {
       q[7] = rec[10]; q[8] = rec[11]; q[9] = rec[12];
     }
   }
+  // training-sample recorder: converged solves only, every rec_every-th solve
+  if (D.rec && npairs > 0 && (res <= Pm.residual_tol || Pm.residual_tol <= 0.f) &&
+      ((long long)st.solves % D.rec_every) == 0) {
+    for (int p = lane; p < npairs; p += 32) {
+      int np = Bc.feat[p] >> 24;
+      const float* pt = Bc.pt + (size_t)p * kMaxPts * kNatPtFloats;
+      for (int k = 0; k < np; ++k) {
+        int slot = atomicAdd(D.rec_count, 1);
+        if (slot >= D.rec_cap) break;
+        float* row = D.rec + (size_t)slot * kRecFloats;
+        const float* f = Bc.x + ((size_t)p * kMaxPts + k) * kFeatures;
+        for (int j = 0; j < kFeatures; ++j) row[j] = f[j];
+        const float* q = pt + k * kNatPtFloats;
+        row[24] = q[7] * inv_imp; row[25] = q[8] * inv_imp; row[26] = q[9] * inv_imp;
+      }
+    }
+  }
 
   // (10) semi-implicit position update and quaternion integration (Eq. quat_int)
   for (int i = lane; i < nb; i += 32) {
@@ -1054,6 +1199,7 @@ __device__ StepOut substep(const Dev& D, const Ep& E, EpState& st, float h) {
   st.ncolours = ncol;
   out.res = res;
   out.sweeps = sweeps;
+  out.predicted = predicted;
   out.npairs = npairs;
   out.npoints = npoints;
   out.ncol = ncol;
@@ -1204,6 +1350,7 @@ __device__ void run_episode(const Dev& D, int e, int mode, int max_steps, unsign
       st.point_steps += o.npoints;
       st.pair_steps += o.npairs;
       st.bp_tests += 0.5 * nact * (nact - 1) + ndyn;
+      st.mlp_points += o.predicted;
     }
     for (int i = lane; i < E.nb; i += 32) {
       int gi = E.b0 + i;
@@ -1537,6 +1684,7 @@ __global__ void stats_kernel(Dev D, jb_episode_stats* out) {
   o.point_steps = st.point_steps;
   o.pair_steps = st.pair_steps;
   o.bp_tests = st.bp_tests;
+  o.mlp_points = st.mlp_points;
   out[e] = o;
 }
 

@@ -1,0 +1,165 @@
+"""Learned warm start: collect samples, train, evaluate, gate.
+
+The network and its training run in the library's kernels (jb_mlp_*): BF16
+tensor-core operands with FP32 accumulation and FP32 master weights.  This
+module only allocates device memory (torch), slices the recorded rows into
+minibatches and drives the calls.  Plain PGS with previous-frame warm start
+is the judge: `evaluate` runs the same episodes with and without the network
+and the gate keeps the network only if it needs fewer sweeps per solve.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+
+import numpy as np
+
+from . import (Batch, check, jb_mlp_bytes, jb_mlp_forward, jb_mlp_grad, jb_mlp_load, jb_mlp_param_count,
+               jb_mlp_save, jb_mlp_scratch_bytes, jb_mlp_train_step, jb_set_recorder, jb_set_warmstart_mlp,
+               _fp)
+
+N_IN, N_HID, N_OUT = 24, 128, 3
+REC = 27
+
+
+def he_init(seed=0):
+    """He-normal weights, zero biases, flat in the layout of jb_mlp_load."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fan_in, shape in ((N_IN, (N_IN, N_HID)), (None, (N_HID,)), (N_HID, (N_HID, N_HID)), (None, (N_HID,)),
+                          (N_HID, (N_HID, N_OUT)), (None, (N_OUT,))):
+        parts.append(rng.normal(0, math.sqrt(2.0 / fan_in), shape).ravel() if fan_in else np.zeros(shape))
+    return np.concatenate(parts).astype(np.float32)
+
+
+class Network:
+    """A network block on the device (jb_mlp_bytes) plus training scratch."""
+
+    def __init__(self, params=None, device="cuda", seed=0):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        self.block = torch.zeros(jb_mlp_bytes(), dtype=torch.uint8, device=self.device)
+        self.nparam = jb_mlp_param_count()
+        self.step_count = 0
+        self._scratch = None
+        self.load(he_init(seed) if params is None else params)
+
+    @property
+    def stream(self):
+        return self.torch.cuda.current_stream(self.device).cuda_stream
+
+    def load(self, params):
+        p = np.ascontiguousarray(params, np.float32)
+        assert p.size == self.nparam
+        check(jb_mlp_load(self.block.data_ptr(), p.ctypes.data_as(_fp), self.stream), "jb_mlp_load")
+        self.step_count = 0
+
+    def params(self):
+        out = np.zeros(self.nparam, np.float32)
+        check(jb_mlp_save(self.block.data_ptr(), out.ctypes.data_as(_fp), self.stream), "jb_mlp_save")
+        return out
+
+    def scratch(self, n):
+        need = jb_mlp_scratch_bytes(int(n))
+        if self._scratch is None or self._scratch.numel() < need:
+            self._scratch = self.torch.empty(need, dtype=self.torch.uint8, device=self.device)
+        return self._scratch
+
+    def forward(self, x):
+        """x: float32 device tensor [n, 24] -> [n, 3]."""
+        x = x.contiguous()
+        n = x.shape[0]
+        y = self.torch.empty((n, N_OUT), dtype=self.torch.float32, device=self.device)
+        sc = self.scratch(n)
+        check(jb_mlp_forward(self.block.data_ptr(), x.data_ptr(), n, y.data_ptr(), sc.data_ptr(), sc.numel(),
+                             self.stream), "jb_mlp_forward")
+        return y
+
+    def grad(self, x, t):
+        x, t = x.contiguous(), t.contiguous()
+        n = x.shape[0]
+        g = self.torch.empty(self.nparam, dtype=self.torch.float32, device=self.device)
+        loss = self.torch.zeros(1, dtype=self.torch.float32, device=self.device)
+        sc = self.scratch(n)
+        check(jb_mlp_grad(self.block.data_ptr(), x.data_ptr(), t.data_ptr(), n, g.data_ptr(), loss.data_ptr(),
+                          sc.data_ptr(), sc.numel(), self.stream), "jb_mlp_grad")
+        return g, loss
+
+    def train_step(self, x, t, lr, wd=1e-4, beta1=0.9, beta2=0.999, eps=1e-8):
+        n = x.shape[0]
+        self.step_count += 1
+        loss = self.torch.zeros(1, dtype=self.torch.float32, device=self.device)
+        sc = self.scratch(n)
+        check(jb_mlp_train_step(self.block.data_ptr(), x.data_ptr(), t.data_ptr(), n, self.step_count,
+                                C.c_float(lr), C.c_float(beta1), C.c_float(beta2), C.c_float(eps), C.c_float(wd),
+                                loss.data_ptr(), sc.data_ptr(), sc.numel(), self.stream), "jb_mlp_train_step")
+        return loss
+
+
+def collect(scene, prot, params, capacity, every=1, max_steps=1 << 30, device="cuda"):
+    """Runs the plain solver through the schedule with the recorder on; returns
+    the recorded rows [n, 27] (device tensor): features, then the converged
+    impulses in units of m_bar |g| h."""
+    import torch
+    prm = dict(params, warm_start=1)
+    b = Batch(scene, prm, max_moves=int(prot.off[-1]), device=device)
+    rows = torch.zeros((capacity, REC), dtype=torch.float32, device=b.device)
+    count = torch.zeros(1, dtype=torch.int32, device=b.device)
+    check(jb_set_recorder(b.h, rows.data_ptr(), capacity, count.data_ptr(), every), "jb_set_recorder")
+    b.set_protocol(prot)
+    b.run_protocol(max_steps)
+    b.sync()
+    n = min(int(count.item()), capacity)
+    return rows[:n]
+
+
+def train(rows, epochs=30, batch=8192, lr=3e-4, wd=1e-4, val_frac=0.2, seed=0, device="cuda", log=None):
+    """AdamW with cosine decay to lr / 20 over `epochs` (the paper's training
+    recipe, Sec. 9.6), 80/20 split of the rows in recorded order; minibatches
+    are contiguous slices from a per-epoch random offset."""
+    n = rows.shape[0]
+    n_val = int(n * val_frac)
+    tr, va = rows[: n - n_val], rows[n - n_val:]
+    x_tr, t_tr = tr[:, :N_IN].contiguous(), tr[:, N_IN:].contiguous()
+    x_va, t_va = va[:, :N_IN].contiguous(), va[:, N_IN:].contiguous()
+    net = Network(device=device, seed=seed)
+    rng = np.random.default_rng(seed)
+    steps_per_epoch = max(1, (x_tr.shape[0] + batch - 1) // batch)
+    total = epochs * steps_per_epoch
+    hist = []
+    it = 0
+    for ep in range(epochs):
+        off = int(rng.integers(0, batch)) if x_tr.shape[0] > batch else 0
+        for s in range(steps_per_epoch):
+            lo = (off + s * batch) % max(1, x_tr.shape[0] - batch + 1) if x_tr.shape[0] > batch else 0
+            hi = min(x_tr.shape[0], lo + batch)
+            cur = lr / 20 + 0.5 * (lr - lr / 20) * (1 + math.cos(math.pi * it / total))
+            net.train_step(x_tr[lo:hi], t_tr[lo:hi], cur, wd)
+            it += 1
+        tl = float(net.grad(x_tr[: min(len(x_tr), 65536)], t_tr[: min(len(x_tr), 65536)])[1].item())
+        vl = float(net.grad(x_va, t_va)[1].item()) if len(x_va) else float("nan")
+        hist.append((ep, tl, vl))
+        if log:
+            log(f"epoch {ep} train {tl:.4g} val {vl:.4g}")
+    return net, hist
+
+
+def evaluate(scene, prot, params, net, mode=2, max_steps=1 << 30, device="cuda"):
+    """Sweeps per solve and body-steps of the plain solver and of the learned
+    warm start (mode 2: unmatched points; 3: all points) on the same episodes,
+    and whether the gate keeps the network."""
+    out = {}
+    for name, ws in (("plain", 1), ("learned", mode)):
+        b = Batch(scene, dict(params, warm_start=ws), max_moves=int(prot.off[-1]), device=device)
+        if ws >= 2:
+            check(jb_set_warmstart_mlp(b.h, net.block.data_ptr()), "jb_set_warmstart_mlp")
+        b.set_protocol(prot)
+        b.run_protocol(max_steps)
+        st = b.stats()
+        out[name] = dict(sweeps_per_solve=float(st["total_sweeps"].sum() / max(st["solves"].sum(), 1)),
+                         body_steps=float(st["body_steps"].sum()),
+                         not_converged=int(((st["status"] & 2) != 0).sum()))
+    out["gain"] = out["plain"]["sweeps_per_solve"] / max(out["learned"]["sweeps_per_solve"], 1e-9)
+    out["keep"] = out["gain"] > 1.0
+    return out

@@ -1,0 +1,165 @@
+"""Warm-start network on the GPU (BF16 tensor-core operands, FP32
+accumulation) against the FP64 oracle network, and the learned warm start in
+the episode kernel.
+
+Tolerances (BF16 operands carry 8 mantissa bits): forward outputs within 2e-2
+relative (Frobenius); gradients with cosine similarity > 0.99 per tensor and
+the loss within 2e-2 relative; AdamW on an exact FP32 gradient within 1e-6
+relative; recorded features within 2e-3 (they are normalised to O(1))."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import mlp as omlp
+
+pytestmark = pytest.mark.gpu
+
+
+def jb():
+    import paper_2606_28394_gb300 as m
+    return m
+
+
+def ws():
+    from paper_2606_28394_gb300 import warmstart
+    return warmstart
+
+
+def features_like(rng, n):
+    X = rng.normal(0, 1, (n, 24))
+    X[:, 4:10] = rng.normal(0, 1, (n, 6))
+    X[:, 22:24] = rng.integers(0, 2, (n, 2))
+    return X
+
+
+def to_dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).to("cuda:0")
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+
+
+def test_forward_matches_fp64_oracle(cuda_device):
+    rng = np.random.default_rng(0)
+    theta = omlp.init(2).astype(np.float32)
+    theta[omlp.N_IN * 128:omlp.N_IN * 128 + 128] = rng.normal(0, 0.1, 128)   # b1
+    net = ws().Network(theta)
+    for n in (1, 15, 16, 17, 1000):
+        X = features_like(rng, n).astype(np.float32)
+        y = net.forward(to_dev(X)).cpu().numpy()
+        yr, _ = omlp.forward(theta.astype(np.float64), X.astype(np.float64))
+        assert rel(y, yr) < 2e-2, (n, rel(y, yr))
+
+
+def test_gradients_match_fp64_oracle(cuda_device):
+    rng = np.random.default_rng(1)
+    theta = omlp.init(3).astype(np.float32) * 0.8
+    net = ws().Network(theta)
+    X = features_like(rng, 3001).astype(np.float32)
+    T = rng.normal(0, 1, (3001, 3)).astype(np.float32)
+    g, loss = net.grad(to_dev(X), to_dev(T))
+    g = g.cpu().numpy()
+    gr, lr = omlp.grad(theta.astype(np.float64), X.astype(np.float64), T.astype(np.float64))
+    assert abs(float(loss.item()) - lr) / lr < 2e-2
+    o = 0
+    for name, shape in omlp.SHAPES:
+        k = int(np.prod(shape))
+        a, b = g[o:o + k], gr[o:o + k]
+        cos = a @ b / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-30)
+        assert cos > 0.99, (name, cos)
+        o += k
+
+
+def test_adamw_step_matches_formula(cuda_device):
+    import torch
+    rng = np.random.default_rng(2)
+    theta = omlp.init(4).astype(np.float32)
+    net = ws().Network(theta)
+    g = rng.normal(size=omlp.N_PARAM).astype(np.float32)
+    gd = to_dev(g)
+    lr, wd = 1e-3, 1e-2
+    for step in (1, 2):
+        jb().check(jb().jb_mlp_adamw(net.block.data_ptr(), gd.data_ptr(), step, C.c_float(lr), C.c_float(0.9),
+                                     C.c_float(0.999), C.c_float(1e-8), C.c_float(wd),
+                                     torch.cuda.current_stream().cuda_stream))
+    got = net.params().astype(np.float64)
+    t = theta.astype(np.float64)
+    m = v = np.zeros_like(t)
+    for step in (1, 2):
+        t, m, v = omlp.adamw(t, g.astype(np.float64), m, v, step, lr, wd=wd)
+    assert rel(got, t) < 1e-6
+
+
+def test_training_fits_a_teacher_network(cuda_device):
+    rng = np.random.default_rng(3)
+    teacher = omlp.init(10) * 0.5
+    X = features_like(rng, 40000)
+    T, _ = omlp.forward(teacher, X)
+    rows = to_dev(np.hstack([X, T]).astype(np.float32))
+    net, hist = ws().train(rows, epochs=12, batch=4096, lr=2e-3, seed=1)
+    assert hist[-1][2] < 0.3 * hist[0][2], hist
+
+
+def test_recorded_features_match_oracle(cuda_device):
+    import torch
+    scene = synth.perturbed(synth.build_scene([synth.Tower(levels=4, mu=0.5)], 1), 5, dx=2e-4, dang=0.01)
+    prm = synth.params(residual_tol=1e-6, pgs_iter_cap=200000)
+    b = jb().Batch(scene, prm)
+    cap = 4096
+    rows = torch.zeros((cap, 27), dtype=torch.float32, device="cuda:0")
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda:0")
+    jb().check(jb().jb_set_recorder(b.h, rows.data_ptr(), cap, cnt.data_ptr(), 1))
+    b.step(1)
+    g = rows[: int(cnt.item())].cpu().numpy().astype(np.float64)
+    s64 = synth.Scene(scene.body_off, *[getattr(scene, k).astype(np.float64) for k in
+                                        ("half", "mass", "mu", "x", "q", "v", "w", "ground_mu")])
+    w = oracle.World(s64, prm)
+    w.set_recorder(cap, 1)
+    w.step(1)
+    o = w.recorded()
+    assert len(g) == len(o) > 0
+    key = lambda r: np.lexsort(np.round(r[:, :24], 2).T[::-1])
+    gf, of = g[key(g), :24], o[key(o), :24]
+    assert np.abs(gf - of).max() < 2e-3, np.abs(gf - of).max()
+
+
+@pytest.mark.parametrize("mode", [2, 3])
+def test_learned_warm_start_converges_to_the_same_state(cuda_device, mode):
+    """Whatever the network predicts, the projected starting impulses only
+    change where Gauss-Seidel starts: the converged state matches the oracle
+    as for plain PGS (both at residual 1e-6)."""
+    scene = synth.perturbed(synth.build_scene([synth.Tower(levels=4, mu=0.5)], 1), 5, dx=2e-4, dang=0.01)
+    prm = synth.params(residual_tol=1e-6, pgs_iter_cap=200000, warm_start=mode)
+    net = ws().Network(omlp.init(7).astype(np.float32) * 0.05)
+    b = jb().Batch(scene, prm)
+    jb().check(jb().jb_set_warmstart_mlp(b.h, net.block.data_ptr()))
+    b.step(3)
+    st = b.stats()
+    assert st["status"][0] == 0 and st["last_residual"][0] <= 1e-6
+    x, q, v, w = b.state()
+    # oracle from the GPU's state after two steps, one more step each
+    b2 = jb().Batch(scene, prm)
+    jb().check(jb().jb_set_warmstart_mlp(b2.h, net.block.data_ptr()))
+    b2.step(2)
+    xs, qs, vs, wsv = b2.state()
+    s64 = synth.Scene(scene.body_off, *[getattr(scene, k).astype(np.float64) for k in
+                                        ("half", "mass", "mu", "x", "q", "v", "w", "ground_mu")])
+    o = oracle.World(s64, dict(prm, warm_start=1))
+    o.set_state(xs.astype(float), qs.astype(float), vs.astype(float), wsv.astype(float))
+    o.step(1)
+    xo, qo, vo, wo = o.state()
+    assert np.abs(x - xo).max() < 1e-5
+    diag = np.sqrt((scene.half.astype(float) ** 2).sum(0))
+    assert np.abs(v - vo).max() < 1e-4 and (np.abs(w - wo).max(0) * diag).max() < 1e-4
+
+
+def test_learned_warm_start_without_network_is_refused(cuda_device):
+    scene = synth.build_scene([synth.Tower(levels=2)], 0)
+    b = jb().Batch(scene, synth.params(warm_start=2))
+    with pytest.raises(jb().JBError):
+        b.step(1)
