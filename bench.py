@@ -62,6 +62,9 @@ def parse():
                     help="fixed-sweep mode with this many sweeps per solve (profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="friction", choices=["friction", "ragged"],
+                    help="friction: 450 x 18-level towers (the headline); ragged: 4096 towers of 6-30 levels")
+    ap.add_argument("--autotune", action="store_true", help="pick smem_pair_factor and residual_every by trials")
     ap.add_argument("--warm-start", default="learned", choices=["learned", "plain"],
                     help="learned: train the warm-start network first and keep it if the gate passes")
     ap.add_argument("--train-episodes", type=int, default=96)
@@ -73,8 +76,14 @@ def parse():
     return ap.parse_args()
 
 
+def make_workload(kind, seed):
+    if kind == "ragged":
+        return synth.ragged_workload(seed=seed)
+    return synth.friction_workload(seed=seed)
+
+
 def workload(args, rank):
-    scene, prot, prm = synth.friction_workload(seed=1 + rank)
+    scene, prot, prm = make_workload(getattr(args, "workload", "friction"), (2 if getattr(args, "workload", "friction") == "ragged" else 1) + rank)
     if args.episodes:
         # spread the subset over the three friction levels
         E = scene.n_episodes
@@ -109,14 +118,14 @@ def prepare_learned(args, rank, prm, device):
     from paper_2606_28394_gb300 import warmstart as ws
     import torch
     t0 = time.perf_counter()
-    sc, pr, _ = synth.friction_workload(seed=3001 + rank)
+    sc, pr, _ = make_workload(args.workload, 3001 + rank)
     s_tr, p_tr = synth.subset(sc, pr, np.linspace(0, sc.n_episodes - 1, args.train_episodes).round().astype(int))
     rows = ws.collect(s_tr, p_tr, prm, capacity=args.train_rows, every=2, max_steps=args.train_steps, device=device)
     t1 = time.perf_counter()
     net, hist = ws.train(rows, epochs=30, batch=8192, lr=3e-4, wd=1e-4, device=device)
     torch.cuda.synchronize(device)
     t2 = time.perf_counter()
-    sc2, pr2, _ = synth.friction_workload(seed=4001 + rank)
+    sc2, pr2, _ = make_workload(args.workload, 4001 + rank)
     s_ev, p_ev = synth.subset(sc2, pr2, np.linspace(0, sc2.n_episodes - 1, args.gate_episodes).round().astype(int))
     gate = ws.evaluate(s_ev, p_ev, prm, net, mode=2, max_steps=args.train_steps, device=device)
     t3 = time.perf_counter()
@@ -263,6 +272,11 @@ def main():
                                                     "remove", "push_steps", "settle_steps")))
     d2h = scene.n_episodes * jb.C.sizeof(jb.jb_episode_stats)
 
+    tuning = None
+    if args.autotune:
+        from paper_2606_28394_gb300 import autotune
+        prm, table = autotune.tune(scene, prot, prm, device=dev)
+        tuning = {"choice": {k: prm[k] for k in ("smem_pair_factor", "residual_every")}, "trials": table}
     net, learned = None, None
     if args.warm_start == "learned":
         net, learned = prepare_learned(args, rank, prm, dev)
@@ -339,8 +353,10 @@ def main():
             "value": value, "unit": "body-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": ("450 episodes x 18-level towers, mu {0.25,0.40,0.60} x 150, removal rounds"
-                                    if not args.episodes else f"{args.episodes} of the 450 episodes")
+            "config": {"workload": (("450 episodes x 18-level towers, mu {0.25,0.40,0.60} x 150, removal rounds"
+                                     if args.workload == "friction" else
+                                     "4096 episodes, levels U{6..30}, mu U[0.2,0.7], removal rounds")
+                                    if not args.episodes else f"{args.episodes} episodes of the {args.workload} workload")
                                    + (f", fixed {args.fixed_iters} sweeps (profiling)" if args.fixed_iters else ""),
                        "residual_tol": args.tol, "pgs_iter_cap": args.cap, "max_steps": args.max_steps,
                        "l2": "flushed (256 MB write) before every timed step",
@@ -350,6 +366,7 @@ def main():
                            if run_prm["warm_start"] >= 2 else "plain (previous-frame)",
                            "training": learned, "plain_judge": plain,
                            "learned_over_plain": (value / plain["value"]) if plain else None},
+            "autotune": tuning,
             "roofline": roof, "gpu_launches": args.steps, "clocks": clk.summary(),
             "e2e": e2e,
             "solver": {"sweeps_per_solve": float(st["total_sweeps"].sum() / max(st["solves"].sum(), 1)),

@@ -95,6 +95,9 @@ typedef struct {
   float collapse_theta_deg; /* Eq. collapse theta_th, degrees */
   float rest_ek;            /* Sec. 8.3 rest threshold, J */
   int32_t rest_steps;       /* Sec. 8.3 step budget after collapse */
+  float smem_pair_factor;   /* shared-memory solver capacity per episode: factor * bodies + 16
+                               contact pairs (0 = 4); steps with more pairs use global memory.
+                               Read at batch creation. */
 } jb_solver_params;
 
 /* Initial scene: host arrays, B = body_off[n_episodes] bodies. */

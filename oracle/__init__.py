@@ -79,6 +79,7 @@ def lib():
         L.or_com_imbalance.restype = C.c_double
         L.or_active.argtypes = [vp, C.c_int]
         L.or_sat.argtypes = [dp, dp, dp, dp, dp, dp, C.c_double, dp, ip, ip, dp, dp]
+        L.or_sat_select.argtypes = [dp, ip, dp]
         L.or_pair_manifold.argtypes = [dp, dp, dp, dp, dp, dp, C.c_double, dp]
         L.or_ground_manifold.argtypes = [dp, dp, dp, C.c_double, dp]
         L.or_rotmat.argtypes = [dp, dp]
@@ -204,6 +205,38 @@ def sat(xA, qA, hA, xB, qB, hB, margin=1e-3):
                    valid.ctypes.data_as(C.POINTER(C.c_int)), axis.ctypes.data_as(C.POINTER(C.c_int)),
                    n.ctypes.data_as(C.POINTER(C.c_double)), dmin.ctypes.data_as(C.POINTER(C.c_double)))
     return dict(hit=bool(hit), delta=delta, valid=valid.astype(bool), axis=int(axis[0]), n=n, dmin=float(dmin[0]))
+
+
+def sat_select(delta, valid):
+    """Stage entry point: the SAT axis choice (tolerant ties, edge rule) on
+    given separations of the 15 axes; returns (axis, dmin)."""
+    d = np.ascontiguousarray(delta, np.float64)
+    v = np.ascontiguousarray(valid, np.int32)
+    dmin = np.zeros(1)
+    ax = lib().or_sat_select(d.ctypes.data_as(C.POINTER(C.c_double)), v.ctypes.data_as(C.POINTER(C.c_int)),
+                             dmin.ctypes.data_as(C.POINTER(C.c_double)))
+    return int(ax), float(dmin[0])
+
+
+def sat_decisions_clear(scene, margin=1e-3, eps=3e-7, trials=300, seed=0):
+    """True when no discrete contact decision of the scene's box pairs is
+    within eps of flipping: no pair separation within 10 eps of -margin, and
+    no pair whose chosen SAT axis changes when its 15 separations move by
+    up to +-eps (random sign patterns).  Inputs that pass have the same
+    contact features in any precision whose separation error is below eps."""
+    rng = np.random.default_rng(seed)
+    P = rng.integers(-1, 2, (trials, 15)) * eps
+    X, Q, H = (np.asarray(getattr(scene, k), np.float64) for k in ("x", "q", "half"))
+    bo = scene.body_off
+    for e in range(len(bo) - 1):
+        for a in range(bo[e], bo[e + 1]):
+            for b in range(a + 1, bo[e + 1]):
+                r = sat(X[:, a], Q[:, a], H[:, a], X[:, b], Q[:, b], H[:, b], margin)
+                if abs(r["dmin"] + margin) < 10 * eps:
+                    return False
+                if r["hit"] and any(sat_select(r["delta"] + p, r["valid"])[0] != r["axis"] for p in P):
+                    return False
+    return True
 
 
 def _crec_dict(rec):

@@ -1257,6 +1257,10 @@ static void mkbox(const double* x, const double* q, const double* h, box_t* b) {
   rotmat(qq, b->R);
 }
 
+int or_sat_select(const double* delta15, const int* valid15, double* dmin) {
+  return sat_select(delta15, valid15, dmin);
+}
+
 int or_sat(const double* xA, const double* qA, const double* hA, const double* xB, const double* qB,
            const double* hB, double margin, double* delta15, int* valid15, int* axis, double* n, double* dmin) {
   box_t A, B; mkbox(xA, qA, hA, &A); mkbox(xB, qB, hB, &B);

@@ -92,6 +92,8 @@ int or_active(const or_world* W, int body);
 int or_sat(const double* xA, const double* qA, const double* hA,
            const double* xB, const double* qB, const double* hB, double margin,
            double* delta15, int* valid15, int* axis, double* n, double* dmin);
+/* the axis choice alone, on given separations (15 axes, validity flags) */
+int or_sat_select(const double* delta15, const int* valid15, double* dmin);
 int or_pair_manifold(const double* xA, const double* qA, const double* hA,
                      const double* xB, const double* qB, const double* hB,
                      double margin, double* out /* OR_CREC */);

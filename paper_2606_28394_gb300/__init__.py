@@ -41,7 +41,8 @@ class jb_solver_params(C.Structure):
                 ("gravity", C.c_float * 3), ("warm_start", C.c_int32),
                 ("match_radius", C.c_float), ("fall_frac", C.c_float),
                 ("collapse_ek", C.c_float), ("collapse_theta_deg", C.c_float),
-                ("rest_ek", C.c_float), ("rest_steps", C.c_int32)]
+                ("rest_ek", C.c_float), ("rest_steps", C.c_int32),
+                ("smem_pair_factor", C.c_float)]
 
 
 _fp = C.POINTER(C.c_float)
@@ -321,3 +322,4 @@ def contacts_as_arrays(contacts):
         out["p"][i] = list(c.p); out["n"][i] = list(c.n); out["t1"][i] = list(c.t1)
         out["lam"][i] = list(c.lambda_)
     return out
+

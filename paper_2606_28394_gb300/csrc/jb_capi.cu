@@ -58,8 +58,24 @@ struct jb_batch {
   std::vector<int64_t> pair_off;
   int32_t* cmd;          // staging for host commands (6 * B ints)
   jb_episode_stats* stats;
-  int grid;              // persistent grid size
   bool has_protocol;
+  // Episodes grouped by size: each class has its own shared-memory plan,
+  // persistent grid and work queue (a slice of the size-sorted order), and
+  // the classes run concurrently on side streams joined to the batch stream.
+  struct SizeClass {
+    int first, count, nb_max, pc_max, ps, smem, grid;
+    cudaStream_t stream;
+    cudaEvent_t join;
+  };
+  std::vector<SizeClass> cls;
+  cudaEvent_t fork = nullptr;
+  ~jb_batch() {
+    for (auto& k : cls) {
+      if (k.stream) cudaStreamDestroy(k.stream);
+      if (k.join) cudaEventDestroy(k.join);
+    }
+    if (fork) cudaEventDestroy(fork);
+  }
 };
 
 // ------------------------------------------------------------ arena layout
@@ -129,7 +145,7 @@ size_t carve(unsigned char* base, const Sizes& z, Dev& D, size_t* persist, int32
     c.nat_x = a.take<float>((size_t)P * kMaxPts * kFeatures);
   }
   if (persist) *persist = (a.off + 255) & ~size_t(255);
-  D.work_counter = a.take<int32_t>(1);
+  D.work_counter = a.take<int32_t>(kMaxSizeClasses);
   int32_t* c = a.take<int32_t>(6 * (size_t)std::max(B, 1));
   jb_episode_stats* s = a.take<jb_episode_stats>(E);
   if (cmd) *cmd = c;
@@ -342,17 +358,46 @@ jb_status jb_batch_create(const jb_scene* sc, const jb_solver_params* p, int32_t
   cudaStream_t s = bt->stream;
   auto fin = [&](jb_status st) { if (st != JB_OK) delete bt; return st; };
 #define CUF(call) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) return fin(fail(JB_ECUDA, "%s: %s", #call, cudaGetErrorString(e_))); } while (0)
-  int dev = 0, nsm = 0, occ = 0;
+  int dev = 0, nsm = 0;
   CUF(cudaGetDevice(&dev));
   CUF(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  int smem = kWarpsPerCta * D.smem_per_warp;
   int smem_max = 0;
   CUF(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  if (smem > smem_max) return fin(fail(JB_EINVAL, "towers too large for shared memory (%d > %d bytes)", smem, smem_max));
-  CUF(cudaFuncSetAttribute(episode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  CUF(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, episode_kernel, kWarpsPerCta * 32, smem));
-  if (occ < 1) return fin(fail(JB_EINVAL, "episode kernel cannot be resident with %d bytes of shared memory", smem));
-  bt->grid = std::max(1, std::min((int)grid_of(z.E, kWarpsPerCta), occ * nsm));
+  // size classes: a new class starts where a tower has at most half the
+  // bodies of the current class's largest (order is size-descending)
+  {
+    const float factor = p->smem_pair_factor > 0.f ? p->smem_pair_factor : 4.f;
+    int smem_all = 0;
+    for (int i = 0; i < z.E;) {
+      jb_batch::SizeClass k{};
+      k.first = i;
+      k.nb_max = sc->body_off[order[i] + 1] - sc->body_off[order[i]];
+      int j = i;
+      const bool last = (int)bt->cls.size() == kMaxSizeClasses - 1;
+      while (j < z.E && (last || 2 * (sc->body_off[order[j] + 1] - sc->body_off[order[j]]) > k.nb_max)) ++j;
+      k.count = j - i;
+      k.pc_max = pair_capacity(k.nb_max);
+      k.ps = std::min(k.pc_max, (int)(factor * k.nb_max) + 16);
+      k.smem = kWarpsPerCta * smem_plan(k.nb_max, k.pc_max, k.ps).bytes;
+      smem_all = std::max(smem_all, k.smem);
+      bt->cls.push_back(k);
+      i = j;
+    }
+    if (smem_all > smem_max)
+      return fin(fail(JB_EINVAL, "towers too large for shared memory (%d > %d bytes)", smem_all, smem_max));
+    CUF(cudaFuncSetAttribute(episode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_all));
+    for (auto& k : bt->cls) {
+      int oc = 0;
+      CUF(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oc, episode_kernel, kWarpsPerCta * 32, k.smem));
+      if (oc < 1) return fin(fail(JB_EINVAL, "episode kernel cannot be resident with %d bytes of shared memory", k.smem));
+      k.grid = std::max(1, std::min((int)grid_of(k.count, kWarpsPerCta), oc * nsm));
+      if (bt->cls.size() > 1) {
+        CUF(cudaStreamCreateWithFlags(&k.stream, cudaStreamNonBlocking));
+        CUF(cudaEventCreateWithFlags(&k.join, cudaEventDisableTiming));
+      }
+    }
+    if (bt->cls.size() > 1) CUF(cudaEventCreateWithFlags(&bt->fork, cudaEventDisableTiming));
+  }
   const size_t fb = sizeof(float);
   CUF(cudaMemcpyAsync((void*)D.body_off, sc->body_off, sizeof(int32_t) * (z.E + 1), cudaMemcpyHostToDevice, s));
   CUF(cudaMemcpyAsync((void*)D.pair_off, poff.data(), sizeof(int64_t) * (z.E + 1), cudaMemcpyHostToDevice, s));
@@ -447,9 +492,28 @@ static jb_status launch_episodes(jb_batch* b, int mode, int n) {
   if (D.P.warm_start >= 2 && !D.mlp)
     return fail(JB_ESTATE, "learned warm start selected but no network set (jb_set_warmstart_mlp)");
   cudaStream_t s = b->stream;
-  CU(cudaMemsetAsync(D.work_counter, 0, sizeof(int32_t), s));
-  episode_kernel<<<b->grid, kWarpsPerCta * 32, kWarpsPerCta * D.smem_per_warp, s>>>(D, mode, n);
-  CU(cudaGetLastError());
+  const bool multi = b->cls.size() > 1;
+  CU(cudaMemsetAsync(D.work_counter, 0, sizeof(int32_t) * kMaxSizeClasses, s));
+  if (multi) CU(cudaEventRecord(b->fork, s));
+  for (size_t c = 0; c < b->cls.size(); ++c) {
+    const auto& k = b->cls[c];
+    Dev Dc = D;
+    Dc.E = k.count;
+    Dc.order = D.order + k.first;
+    Dc.nb_max = k.nb_max;
+    Dc.pc_max = k.pc_max;
+    Dc.ps = k.ps;
+    Dc.smem_per_warp = k.smem / kWarpsPerCta;
+    Dc.work_counter = D.work_counter + c;
+    cudaStream_t ks = multi ? k.stream : s;
+    if (multi) CU(cudaStreamWaitEvent(ks, b->fork, 0));
+    episode_kernel<<<k.grid, kWarpsPerCta * 32, k.smem, ks>>>(Dc, mode, n);
+    CU(cudaGetLastError());
+    if (multi) {
+      CU(cudaEventRecord(k.join, ks));
+      CU(cudaStreamWaitEvent(s, k.join, 0));
+    }
+  }
   return JB_OK;
 }
 

@@ -10,6 +10,7 @@
 namespace jbk {
 
 constexpr int kWarpsPerCta = 1;          // one warp (episode) per CTA
+constexpr int kMaxSizeClasses = 4;       // episode size classes per batch
 constexpr int kMaxColours = 64;          // colour kSerial is solved by one lane
 constexpr int kSerial = kMaxColours - 1;
 constexpr int kMaxPts = 4;               // points per pair (Sec. 6.2.1, step d)

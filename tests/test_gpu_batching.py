@@ -1,0 +1,74 @@
+"""Ragged batches: episodes of different sizes run in size classes (own
+shared-memory plan, grid and work queue, concurrent streams).  Classes only
+schedule: every episode's trajectory is bit-identical to running it alone.
+The autotuner returns one of its candidate configurations."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def jb():
+    import paper_2606_28394_gb300 as m
+    return m
+
+
+def test_size_classes_do_not_change_results(cuda_device):
+    levels = [25, 4, 13, 6, 18, 9]
+    towers = [synth.Tower(levels=l, mu=0.3 + 0.05 * i) for i, l in enumerate(levels)]
+    scene = synth.perturbed(synth.build_scene(towers, 21), 22, dx=1e-4, dang=0.005)
+    prm = synth.params(residual_tol=1e-5, pgs_iter_cap=20000)
+    b = jb().Batch(scene, prm)
+    b.step(6)
+    x, q, v, w = b.state()
+    st = b.stats()
+    for e in range(len(towers)):
+        one = synth.subset(scene, synth._protocol([[]] * len(towers), len(towers)), [e])[0]
+        a = jb().Batch(one, prm)
+        a.step(6)
+        xe, qe, ve, we = a.state()
+        lo, hi = scene.body_off[e], scene.body_off[e + 1]
+        for big, small in ((x, xe), (q, qe), (v, ve), (w, we)):
+            assert np.array_equal(big[:, lo:hi], small), e
+        assert a.stats()["total_sweeps"][0] == st["total_sweeps"][e]
+
+
+def test_autotuner_returns_a_candidate(cuda_device):
+    from paper_2606_28394_gb300 import autotune
+    scene, prot, prm = synth.ragged_workload(seed=7, n=16)
+    prm = dict(prm, residual_tol=1e-5, pgs_iter_cap=5000)
+    tuned, table = autotune.tune(scene, prot, prm, trial_steps=8, sample=8, use_cache=False)
+    assert tuned["smem_pair_factor"] in autotune.FACTORS and tuned["residual_every"] in autotune.EVERY
+    assert len(table) == len(autotune.FACTORS) * len(autotune.EVERY)
+    assert all(r["ms"] > 0 for r in table)
+
+
+def test_ragged_batch_one_step_parity(cuda_device):
+    """Towers of 3, 7, 12 and 5 levels (three size classes) in one batch, one
+    step at PGS residual 1e-6 on both sides: the same bounds as the
+    single-tower parity cases."""
+    towers = [synth.Tower(levels=l, mu=m) for l, m in ((3, 0.3), (7, 0.5), (12, 0.4), (5, 0.6))]
+    scene = synth.perturbed(synth.build_scene(towers, 4), 13, dx=2e-4, dang=0.01)
+    # FP32 and FP64 may take a near-tied SAT axis choice differently (a
+    # different, equally valid manifold); the jitter seed is one whose
+    # decisions are all clear by 3e-7 m (most seeds have one or two pairs
+    # within that of the 10 um tie or the edge-rule threshold).
+    assert oracle.sat_decisions_clear(scene)
+    prm = synth.params(residual_tol=1e-6, pgs_iter_cap=200000)
+    b = jb().Batch(scene, prm)
+    s64 = synth.Scene(scene.body_off, *[getattr(scene, k).astype(np.float64) for k in
+                                        ("half", "mass", "mu", "x", "q", "v", "w", "ground_mu")])
+    w = oracle.World(s64, prm)
+    b.step(1)
+    w.step(1)
+    st, so = b.stats(), w.stats()
+    assert (st["status"] == 0).all() and (st["last_residual"] <= 1e-6).all()
+    assert (so["last_residual"] <= 1e-6).all()
+    xg, qg, vg, wg = b.state()
+    xo, qo, vo, wo = w.state()
+    assert np.abs(xg - xo).max() < 1e-5
+    diag = np.sqrt((scene.half.astype(float) ** 2).sum(0))
+    assert np.abs(vg - vo).max() < 1e-4 and (np.abs(wg - wo).max(0) * diag).max() < 1e-4

@@ -469,3 +469,65 @@ def test_flush_tower_manifolds_are_exact_rectangles():
             n_cross += 1
             assert np.allclose(ext, [0, Wd, Wd], atol=3e-6)
     assert (n_ground, n_side, n_cross) == (3, 36, 153)
+
+
+def test_sat_axis_choice_rule():
+    """The axis choice on given separations (reading of Sec. 6.2): a later
+    face axis replaces the best only when smaller by more than 10 um; a cross
+    axis wins only when below the best face by 5 % of it plus 10 um; invalid
+    cross axes never win; the contact depth is the minimum over valid axes."""
+    tie = 1e-5
+    valid = np.ones(15, np.int32)
+    d = np.full(15, 1e-3)
+    assert oracle.sat_select(d, valid)[0] == 0                 # all equal: first face
+    d2 = d.copy(); d2[4] = d[0] - 2 * tie
+    assert oracle.sat_select(d2, valid)[0] == 4
+    d2[4] = d[0] - 0.5 * tie
+    assert oracle.sat_select(d2, valid)[0] == 0                # within the tie
+    thr = 0.05 * 1e-3 + tie
+    d3 = d.copy(); d3[9] = d[0] - thr - 1e-7
+    ax, dmin = oracle.sat_select(d3, valid)
+    assert ax == 9 and dmin == d3[9]
+    d3[9] = d[0] - thr + 1e-7
+    ax, dmin = oracle.sat_select(d3, valid)
+    assert ax == 0 and dmin == d3[9]                           # depth from the edge axis all the same
+    v2 = valid.copy(); v2[9] = 0
+    d3[9] = -1.0
+    assert oracle.sat_select(d3, v2) == (0, 1e-3)              # invalid (parallel edges) ignored
+
+
+def test_decision_guard_flags_a_near_tie():
+    """Block B crossed on block A and tilted by phi about world x: B's face
+    axis takes over from A's once their separations differ by the 10 um tie
+    (about 0.025 phi here).  At the flip angle the guard reports an unclear
+    decision; at half or twice that angle, and untilted, the pair is clear."""
+    h = (0.0375, 0.0125, 0.0075)
+
+    def scene(phi):
+        c, s_ = np.cos(phi / 2), np.sin(phi / 2)
+        r = np.sqrt(0.5)
+        q = (c * r, s_ * r, -s_ * r, c * r)          # tilt about world x after 90 deg about z
+        sc = synth.custom_scene([dict(half=h, x=(0, 0, 0.0075), mass=0.0, mu=0.4),
+                                 dict(half=h, x=(0, 0, 0.0225 - 2e-4), q=q, mass=0.015, mu=0.4)],
+                                ground_mu=0.4)
+        sc.q = np.array([[1, 0, 0, 0], q], np.float64).T
+        sc.x, sc.half = sc.x.astype(np.float64), sc.half.astype(np.float64)
+        return sc
+
+    def axis(phi):
+        sc = scene(phi)
+        return oracle.sat(sc.x[:, 0], sc.q[:, 0], sc.half[:, 0], sc.x[:, 1], sc.q[:, 1], sc.half[:, 1])["axis"]
+
+    assert axis(0.0) == 2 and axis(1e-3) == 5
+    lo, hi = 0.0, 1e-3
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        lo, hi = (mid, hi) if axis(mid) == 2 else (lo, mid)
+    assert abs(hi - 4e-4) < 2e-5
+    assert not oracle.sat_decisions_clear(scene(hi))
+    assert oracle.sat_decisions_clear(scene(0.0))
+    assert oracle.sat_decisions_clear(scene(0.5 * hi)) and oracle.sat_decisions_clear(scene(2 * hi))
+    # a gap of exactly the contact margin is unclear as well
+    sc = scene(0.0)
+    sc.x[2, 1] = 0.0225 + 1e-3
+    assert not oracle.sat_decisions_clear(sc)
