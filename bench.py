@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="friction", choices=["friction", "ragged"],
                     help="friction: 450 x 18-level towers (the headline); ragged: 4096 towers of 6-30 levels")
-    ap.add_argument("--autotune", action="store_true", help="pick smem_pair_factor and residual_every by trials")
+    ap.add_argument("--autotune", action="store_true", help="pick smem_pair_factor and the residual-check cadence by trials")
     ap.add_argument("--warm-start", default="learned", choices=["learned", "plain"],
                     help="learned: train the warm-start network first and keep it if the gate passes")
     ap.add_argument("--train-episodes", type=int, default=96)
@@ -276,7 +276,7 @@ def main():
     if args.autotune:
         from paper_2606_28394_gb300 import autotune
         prm, table = autotune.tune(scene, prot, prm, device=dev)
-        tuning = {"choice": {k: prm[k] for k in ("smem_pair_factor", "residual_every")}, "trials": table}
+        tuning = {"choice": {k: prm[k] for k in autotune.TUNED}, "trials": table}
     net, learned = None, None
     if args.warm_start == "learned":
         net, learned = prepare_learned(args, rank, prm, dev)
@@ -359,6 +359,8 @@ def main():
                                     if not args.episodes else f"{args.episodes} episodes of the {args.workload} workload")
                                    + (f", fixed {args.fixed_iters} sweeps (profiling)" if args.fixed_iters else ""),
                        "residual_tol": args.tol, "pgs_iter_cap": args.cap, "max_steps": args.max_steps,
+                       "residual_check_every": [jb.params_from_dict(run_prm).residual_every,
+                                                jb.params_from_dict(run_prm).residual_every_max],
                        "l2": "flushed (256 MB write) before every timed step",
                        "warmup": f"{args.warmup} passes of the job truncated to {args.warmup_steps} physics steps",
                        "episodes": scene.n_episodes, "bodies": scene.n_bodies},

@@ -80,7 +80,7 @@ typedef struct {
   float residual_tol;       /* > 0: residual mode, sweep until residual <= tol (m/s) */
   int32_t pgs_iter_cap;     /* sweep cap in residual mode */
   int32_t pgs_min_iters;    /* sweeps before the first residual check */
-  int32_t residual_every;   /* residual mode: check every this many sweeps (>= 1) */
+  int32_t residual_every;   /* residual mode: at least this many sweeps between checks (>= 1) */
   float restitution;        /* e, applied as (1+e) in the normal row (Sec. 7.1) */
   float beta, slop;         /* Eq. baumgarte */
   float contact_margin;     /* speculative contact margin m_c, m */
@@ -98,6 +98,19 @@ typedef struct {
   float smem_pair_factor;   /* shared-memory solver capacity per episode: factor * bodies + 16
                                contact pairs (0 = 4); steps with more pairs use global memory.
                                Read at batch creation. */
+  float sor;                /* relaxation factor omega of the PGS rows, in (0, 2); 0 = 1, the
+                               paper's plain projected Gauss-Seidel.  Every row takes
+                               proj(lambda - omega (v + b) / k) (projected SOR, Cryer 1971): the
+                               fixed points, and so the converged impulses, do not depend on
+                               omega; the sweeps needed to reach residual_tol do. */
+  int32_t sweep_order;      /* 0: every sweep visits the colours in order; 1: odd sweeps visit
+                               them in reverse (symmetric Gauss-Seidel) */
+  int32_t residual_every_max; /* residual mode: at most this many sweeps between checks.  Above
+                               residual_every, the gap to the next check is half the sweeps
+                               the last two residuals predict are still needed (geometric
+                               decay), clamped to [residual_every, residual_every_max]; a solve
+                               only ends at a check, so this bounds the extra sweeps a
+                               converged solve runs.  0 = residual_every (fixed cadence). */
 } jb_solver_params;
 
 /* Initial scene: host arrays, B = body_off[n_episodes] bodies. */

@@ -42,7 +42,8 @@ class jb_solver_params(C.Structure):
                 ("match_radius", C.c_float), ("fall_frac", C.c_float),
                 ("collapse_ek", C.c_float), ("collapse_theta_deg", C.c_float),
                 ("rest_ek", C.c_float), ("rest_steps", C.c_int32),
-                ("smem_pair_factor", C.c_float)]
+                ("smem_pair_factor", C.c_float), ("sor", C.c_float), ("sweep_order", C.c_int32),
+                ("residual_every_max", C.c_int32)]
 
 
 _fp = C.POINTER(C.c_float)

@@ -3,8 +3,9 @@
 Picks the per-episode shared-memory solver capacity (smem_pair_factor: pairs
 per body kept on chip before a step falls back to global memory, which sets
 how many episodes fit per SM) and the residual-check cadence
-(residual_every) by timing short trials of the actual workload with CUDA
-events: the first `trial_steps` physics steps of a sample of its episodes.
+(residual_every, residual_every_max) by timing short trials of the actual
+workload with CUDA events: the first `trial_steps` physics steps of a sample
+of its episodes.
 Choices are cached in a JSON file keyed by GPU name and a hash of the
 workload's shape and solver parameters.
 """
@@ -22,7 +23,8 @@ from . import Batch
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), ".autotune_cache.json")
 FACTORS = (3.6, 4.0, 5.0)
-EVERY = (2, 4, 8)
+CADENCE = ((4, 4), (4, 32), (2, 32))   # (residual_every, residual_every_max)
+TUNED = ("smem_pair_factor", "residual_every", "residual_every_max")
 
 
 def subset(scene, prot, episodes):
@@ -49,14 +51,15 @@ def subset(scene, prot, episodes):
 def _key(scene, params, gpu):
     h = hashlib.sha1()
     h.update(np.asarray(scene.body_off, np.int64).tobytes())
-    h.update(json.dumps({k: v for k, v in sorted(params.items()) if k not in ("smem_pair_factor", "residual_every")},
+    h.update(json.dumps({k: v for k, v in sorted(params.items()) if k not in TUNED},
                         default=str).encode())
     return f"{gpu}:{h.hexdigest()[:16]}"
 
 
 def tune(scene, prot, params, trial_steps=120, sample=64, device="cuda", use_cache=True, log=None):
     """Returns a copy of params with the fastest (smem_pair_factor,
-    residual_every) on a trial of the workload, and the timing table."""
+    residual_every, residual_every_max) on a trial of the workload, and the
+    timing table."""
     import torch
     gpu = torch.cuda.get_device_name(torch.device(device))
     key = _key(scene, params, gpu)
@@ -70,8 +73,8 @@ def tune(scene, prot, params, trial_steps=120, sample=64, device="cuda", use_cac
     s, p = subset(scene, prot, idx)
     table = []
     for fac in FACTORS:
-        for ev in EVERY:
-            prm = dict(params, smem_pair_factor=fac, residual_every=ev)
+        for ev, evm in CADENCE:
+            prm = dict(params, smem_pair_factor=fac, residual_every=ev, residual_every_max=evm)
             b = Batch(s, prm, max_moves=int(p.off[-1]), device=device)
             b.set_protocol(p)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -80,11 +83,11 @@ def tune(scene, prot, params, trial_steps=120, sample=64, device="cuda", use_cac
             e1.record(b.stream)
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1)
-            table.append({"smem_pair_factor": fac, "residual_every": ev, "ms": ms})
+            table.append({"smem_pair_factor": fac, "residual_every": ev, "residual_every_max": evm, "ms": ms})
             if log:
-                log(f"factor {fac} every {ev}: {ms:.1f} ms")
+                log(f"factor {fac} cadence {ev}..{evm}: {ms:.1f} ms")
     best = min(table, key=lambda r: r["ms"])
-    choice = {"smem_pair_factor": best["smem_pair_factor"], "residual_every": best["residual_every"]}
+    choice = {k: best[k] for k in TUNED}
     if use_cache:
         cache[key] = {"best": choice, "table": table}
         with open(CACHE, "w") as f:

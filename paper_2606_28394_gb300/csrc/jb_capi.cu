@@ -194,6 +194,9 @@ Params to_params(const jb_solver_params* p) {
   q.collapse_cos = cosf(p->collapse_theta_deg * 3.14159265358979f / 180.f);
   q.rest_ek = p->rest_ek;
   q.rest_steps = p->rest_steps;
+  q.sor = p->sor > 0.f ? p->sor : 1.f;
+  q.sweep_order = p->sweep_order;
+  q.residual_every_max = p->residual_every_max > p->residual_every ? p->residual_every_max : p->residual_every;
   return q;
 }
 
@@ -208,6 +211,9 @@ const char* check_params(const jb_solver_params* p) {
   if (!(p->contact_margin >= 0.f) || !(p->aabb_eps >= p->contact_margin))
     return "need 0 <= contact_margin <= aabb_eps";
   if (p->warm_start < 0 || p->warm_start > 3) return "warm_start must be 0, 1, 2 or 3";
+  if (!(p->sor >= 0.f && p->sor < 2.f)) return "sor must be in (0, 2) (0 selects 1)";
+  if (p->sweep_order < 0 || p->sweep_order > 1) return "sweep_order must be 0 or 1";
+  if (p->residual_every_max < 0) return "residual_every_max must be >= 0";
   return nullptr;
 }
 
@@ -233,6 +239,9 @@ void jb_default_params(jb_solver_params* p) {
   p->pgs_iter_cap = 20000;
   p->pgs_min_iters = 1;
   p->residual_every = 4;
+  p->sor = 1.f;
+  p->sweep_order = 0;
+  p->residual_every_max = 32;
   p->restitution = 0.10f;
   p->beta = 0.35f;
   p->slop = 4e-4f;

@@ -57,6 +57,9 @@ struct Params {
   int warm_start;
   float match_radius, fall_frac, collapse_ek, collapse_cos, rest_ek;
   int rest_steps;
+  float sor;        // PGS relaxation factor omega (1 = plain PGS)
+  int sweep_order;  // 1: odd sweeps run the colours in reverse
+  int residual_every_max;  // >= residual_every
 };
 
 // One contact buffer (the batch holds two: this step's and the previous one).

@@ -547,8 +547,12 @@ __device__ __forceinline__ void apply_point(PairRegs& R, float3 rA, float3 rB, f
 // (diagonal: Eq. keff).  The rows therefore run on the three scalar
 // velocities and the bodies take the point's summed impulse once: the same
 // Gauss-Seidel iterate as updating the bodies after every row.
+//
+// Mode 1 relaxes every row by om (projected SOR): the caller folds om into
+// e1 for the normal row; om = 1 is the paper's plain PGS, bit for bit.
 template <int mode, bool kS>
-__device__ __forceinline__ void pair_pass(const SolverView<kS>& V, int sl, float e1, float beta, float slop) {
+__device__ __forceinline__ void pair_pass(const SolverView<kS>& V, int sl, float e1, float om, float beta,
+                                          float slop) {
   if constexpr (mode == 2) {
     uint32_t ab = V.ab[sl];
     int a = ab & 0xffff, b = ab >> 16;
@@ -584,10 +588,10 @@ __device__ __forceinline__ void pair_pass(const SolverView<kS>& V, int sl, float
       v1 += w01 * d0;
       v2 += w02 * d0;
       float lim = R.mu * nl0;
-      float nl1 = fminf(fmaxf(l1 - v1 * ik1, -lim), lim);
+      float nl1 = fminf(fmaxf(l1 - v1 * (om * ik1), -lim), lim);
       float d1 = nl1 - l1;
       v2 += w12 * d1;
-      float nl2 = fminf(fmaxf(l2 - v2 * ik2, -lim), lim);
+      float nl2 = fminf(fmaxf(l2 - v2 * (om * ik2), -lim), lim);
       float d2 = nl2 - l2;
       apply_point(R, rA, rB, d0 * R.n + d1 * R.t1 + d2 * R.t2);
       VSP(10, k) = nl0; VSP(11, k) = nl1; VSP(12, k) = nl2;
@@ -598,7 +602,9 @@ __device__ __forceinline__ void pair_pass(const SolverView<kS>& V, int sl, float
 }
 
 // Residual of one pair at the current state (no update): max over rows of
-// k |proj(lambda - (v + b) / k) - lambda|, k the inverse effective mass.
+// k |proj(lambda - (v + b) / k) - lambda|, k the inverse effective mass.  It
+// only feeds the stopping test and the statistics, so the division by the
+// stored 1/k is the fast approximate one (a few ulp).
 template <bool kS>
 __device__ __forceinline__ float pair_residual(const SolverView<kS>& V, int sl) {
   PairRegs R;
@@ -615,7 +621,8 @@ __device__ __forceinline__ float pair_residual(const SolverView<kS>& V, int sl) 
     float p0 = fmaxf(0.f, l0 - (dot(u, R.n) + bias) * ik0);
     float p1 = fminf(fmaxf(l1 - dot(u, R.t1) * ik1, -lim), lim);
     float p2 = fminf(fmaxf(l2 - dot(u, R.t2) * ik2, -lim), lim);
-    float m = fmaxf(fabsf(p0 - l0) / ik0, fmaxf(fabsf(p1 - l1) / ik1, fabsf(p2 - l2) / ik2));
+    float m = fmaxf(__fdividef(fabsf(p0 - l0), ik0),
+                    fmaxf(__fdividef(fabsf(p1 - l1), ik1), __fdividef(fabsf(p2 - l2), ik2)));
     if (!(m <= r)) r = m;   // keeps NaN
   }
   return r;
@@ -636,19 +643,23 @@ __device__ __noinline__ float episode_residual_t(const SolverRef r, int npairs, 
   return nan ? __int_as_float(0x7fc00000) : warp_max(res);
 }
 
-// Runs `mode` over every colour in order; lanes take the slots of a colour.
-// `off` holds the colour offsets (ncol + 1 entries).
+// Runs `mode` over every colour, in order or (rev) in reverse order; lanes
+// take the slots of a colour.  `off` holds the colour offsets (ncol + 1
+// entries).  Pairs of one colour share no body, so their order is free.
 template <int mode, bool kS>
 __device__ __noinline__ void colour_passes_t(const SolverRef r, const int* __restrict__ off, int ncol, int lane,
-                                             float e1, float beta, float slop) {
+                                             float e1, float om, bool rev, float beta, float slop) {
   const SolverView<kS> V(r);
-  for (int c = 0; c < ncol; ++c) {
+  for (int i = 0; i < ncol; ++i) {
+    const int c = rev ? ncol - 1 - i : i;
     int s0 = off[c], s1 = off[c + 1];
     if (c == kSerial) {
-      if (lane == 0)
-        for (int sl = s0; sl < s1; ++sl) pair_pass<mode>(V, sl, e1, beta, slop);
+      if (lane == 0) {
+        if (rev) for (int sl = s1 - 1; sl >= s0; --sl) pair_pass<mode>(V, sl, e1, om, beta, slop);
+        else for (int sl = s0; sl < s1; ++sl) pair_pass<mode>(V, sl, e1, om, beta, slop);
+      }
     } else {
-      for (int sl = s0 + lane; sl < s1; sl += 32) pair_pass<mode>(V, sl, e1, beta, slop);
+      for (int sl = s0 + lane; sl < s1; sl += 32) pair_pass<mode>(V, sl, e1, om, beta, slop);
     }
     __syncwarp();
   }
@@ -656,9 +667,9 @@ __device__ __noinline__ void colour_passes_t(const SolverRef r, const int* __res
 
 template <int mode>
 __device__ __forceinline__ void colour_passes(const SolverRef& r, const int* off, int ncol, int lane, float e1,
-                                              float beta, float slop) {
-  if (r.shared) colour_passes_t<mode, true>(r, off, ncol, lane, e1, beta, slop);
-  else colour_passes_t<mode, false>(r, off, ncol, lane, e1, beta, slop);
+                                              float om, bool rev, float beta, float slop) {
+  if (r.shared) colour_passes_t<mode, true>(r, off, ncol, lane, e1, om, rev, beta, slop);
+  else colour_passes_t<mode, false>(r, off, ncol, lane, e1, om, rev, beta, slop);
 }
 
 __device__ __forceinline__ float episode_residual(const SolverRef& r, int npairs, int lane) {
@@ -1122,7 +1133,7 @@ __device__ StepOut substep(const Dev& D, const Ep& E, EpState& st, float h) {
   // (8) warm start: apply the inherited impulses
   const SolverRef V = solver_ref(s, Bc);
   const float e1 = 1.f + Pm.restitution;
-  if (Pm.warm_start >= 1) colour_passes<0>(V, s.off, ncol, lane, e1, Pm.beta, Pm.slop);
+  if (Pm.warm_start >= 1) colour_passes<0>(V, s.off, ncol, lane, e1, 1.f, false, Pm.beta, Pm.slop);
 
   // (9) projected Gauss-Seidel sweeps
   int sweeps = 0;
@@ -1131,14 +1142,30 @@ __device__ StepOut substep(const Dev& D, const Ep& E, EpState& st, float h) {
     const bool rmode = Pm.residual_tol > 0.f;
     const int cap = rmode ? Pm.pgs_iter_cap : Pm.pgs_iters;
     const int every = Pm.residual_every > 0 ? Pm.residual_every : 1;
+    const int every_max = Pm.residual_every_max > every ? Pm.residual_every_max : every;
+    const float om = Pm.sor, e1om = Pm.sor * e1;
+    int next = rmode ? Pm.pgs_min_iters : cap;   // sweep count of the next residual check
+    float prev_res = -1.f;
+    int prev_at = 0;
     while (sweeps < cap) {
-      colour_passes<1>(V, s.off, ncol, lane, e1, Pm.beta, Pm.slop);
+      colour_passes<1>(V, s.off, ncol, lane, e1om, om, Pm.sweep_order == 1 && (sweeps & 1), Pm.beta, Pm.slop);
       ++sweeps;
-      bool check = rmode ? (sweeps >= Pm.pgs_min_iters && ((sweeps - Pm.pgs_min_iters) % every == 0 || sweeps == cap))
-                         : (sweeps == cap);
-      if (check) {
+      if (sweeps >= next || sweeps == cap) {
         res = episode_residual(V, npairs, lane);
-        if (rmode && (res <= Pm.residual_tol || !(res == res))) break;
+        if (!rmode || res <= Pm.residual_tol || !(res == res)) break;
+        // check cadence: half the sweeps that the decay rate between the
+        // last two checks predicts are still needed, within [every, every_max]
+        int gap = every_max;
+        if (every_max > every && prev_res > 0.f && res < prev_res) {
+          const float per_sweep = __logf(res / prev_res) / (float)(sweeps - prev_at);
+          const float need = __logf(Pm.residual_tol / res) / per_sweep;
+          gap = need < 2.f * every_max ? max(every, (int)(0.5f * need)) : every_max;
+        } else if (every_max == every || prev_res < 0.f) {
+          gap = every;
+        }
+        prev_res = res;
+        prev_at = sweeps;
+        next = sweeps + gap;
       }
     }
     if (rmode && sweeps >= cap && !(res <= Pm.residual_tol)) out.status |= JB_EP_NOT_CONVERGED;
@@ -1192,7 +1219,7 @@ __device__ StepOut substep(const Dev& D, const Ep& E, EpState& st, float h) {
   __syncwarp();
 
   // (11) position correction (Eq. baumgarte), colour by colour
-  colour_passes<2>(V, s.off, ncol, lane, e1, Pm.beta, Pm.slop);
+  colour_passes<2>(V, s.off, ncol, lane, e1, 1.f, false, Pm.beta, Pm.slop);
 
   st.cur = cur;
   st.npairs = npairs;

@@ -41,8 +41,9 @@ def test_autotuner_returns_a_candidate(cuda_device):
     scene, prot, prm = synth.ragged_workload(seed=7, n=16)
     prm = dict(prm, residual_tol=1e-5, pgs_iter_cap=5000)
     tuned, table = autotune.tune(scene, prot, prm, trial_steps=8, sample=8, use_cache=False)
-    assert tuned["smem_pair_factor"] in autotune.FACTORS and tuned["residual_every"] in autotune.EVERY
-    assert len(table) == len(autotune.FACTORS) * len(autotune.EVERY)
+    assert tuned["smem_pair_factor"] in autotune.FACTORS
+    assert (tuned["residual_every"], tuned["residual_every_max"]) in autotune.CADENCE
+    assert len(table) == len(autotune.FACTORS) * len(autotune.CADENCE)
     assert all(r["ms"] > 0 for r in table)
 
 
