@@ -601,6 +601,93 @@ __device__ __forceinline__ void pair_pass(const SolverView<kS>& V, int sl, float
   if (R.db) { vst3(V, FV, R.b, R.vb); vst3(V, FW, R.b, R.wb); }
 }
 
+// Mode 1 of pair_pass in packed FP32 (FFMA2: two lanes of arithmetic per
+// instruction).  Body A's and body B's copies of each quantity share a
+// float2 (A in .x, B in .y), with A's signs folded in (inverse mass and
+// inverse inertia negated), so that the lever arms, the bodies' point
+// velocities and the impulse application run once for both bodies.  The
+// rows are scalar and identical to pair_pass; the iterate is the same up to
+// rounding order.
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+
+template <bool kS>
+__device__ __forceinline__ void pair_sweep_packed(const SolverView<kS>& V, int sl, float e1, float om) {
+  const uint32_t ab = V.ab[sl];
+  const int a = ab & 0xffff, b = ab >> 16;
+  const float3 n = f3(VSF(0), VSF(1), VSF(2));
+  const float3 t1 = f3(VSF(3), VSF(4), VSF(5));
+  const float3 t2 = cross(n, t1);
+  const float mu = VSF(6);
+  float2 vx = make_float2(VF(FV, a), VF(FV, b)), vy = make_float2(VF(FV + 1, a), VF(FV + 1, b)),
+         vz = make_float2(VF(FV + 2, a), VF(FV + 2, b));
+  float2 wx = make_float2(VF(FW, a), VF(FW, b)), wy = make_float2(VF(FW + 1, a), VF(FW + 1, b)),
+         wz = make_float2(VF(FW + 2, a), VF(FW + 2, b));
+  const float2 xx = make_float2(VF(FX, a), VF(FX, b)), xy = make_float2(VF(FX + 1, a), VF(FX + 1, b)),
+               xz = make_float2(VF(FX + 2, a), VF(FX + 2, b));
+  const float2 im = make_float2(-VF(FM, a), VF(FM, b));
+  const float2 Ixx = make_float2(-VF(FI, a), VF(FI, b)), Iyy = make_float2(-VF(FI + 1, a), VF(FI + 1, b)),
+               Izz = make_float2(-VF(FI + 2, a), VF(FI + 2, b)), Ixy = make_float2(-VF(FI + 3, a), VF(FI + 3, b)),
+               Ixz = make_float2(-VF(FI + 4, a), VF(FI + 4, b)), Iyz = make_float2(-VF(FI + 5, a), VF(FI + 5, b));
+  const bool da = !(V.flags[a] & kStatic), db = !(V.flags[b] & kStatic);
+  const float2 nt_x = make_float2(n.x, t1.x), nt_y = make_float2(n.y, t1.y), nt_z = make_float2(n.z, t1.z);
+  // all kMaxPts point records, unused ones zero (their impulse change is 0):
+  // one branch-free block that the compiler can schedule across points
+#pragma unroll
+  for (int k = 0; k < kMaxPts; ++k) {
+    const float px = VSP(0, k), py = VSP(1, k), pz = VSP(2, k);
+    // lever arms r = p - x and their negatives, both bodies at once
+    const float2 rx = __fadd2_rn(bc2(px), make_float2(-xx.x, -xx.y));
+    const float2 ry = __fadd2_rn(bc2(py), make_float2(-xy.x, -xy.y));
+    const float2 rz = __fadd2_rn(bc2(pz), make_float2(-xz.x, -xz.y));
+    const float2 nrx = __fadd2_rn(xx, bc2(-px)), nry = __fadd2_rn(xy, bc2(-py)), nrz = __fadd2_rn(xz, bc2(-pz));
+    // each body's velocity at the point, v + w x r
+    float2 sx = __ffma2_rn(wy, rz, vx), sy = __ffma2_rn(wz, rx, vy), sz = __ffma2_rn(wx, ry, vz);
+    sx = __ffma2_rn(wz, nry, sx);
+    sy = __ffma2_rn(wx, nrz, sy);
+    sz = __ffma2_rn(wy, nrx, sz);
+    const float ux = sx.y - sx.x, uy = sy.y - sy.x, uz = sz.y - sz.x;
+    // (vn, v1) together, v2 alone
+    float2 q = __fmul2_rn(bc2(ux), nt_x);
+    q = __ffma2_rn(bc2(uy), nt_y, q);
+    q = __ffma2_rn(bc2(uz), nt_z, q);
+    float vn = q.x, v1 = q.y;
+    float v2 = ux * t2.x + uy * t2.y + uz * t2.z;
+    const float ik0 = VSP(3, k), ik1 = VSP(4, k), ik2 = VSP(5, k);
+    const float w01 = VSP(6, k), w02 = VSP(7, k), w12 = VSP(8, k);
+    const float bias = VSP(9, k);
+    const float l0 = VSP(10, k), l1 = VSP(11, k), l2 = VSP(12, k);
+    float nl0 = fmaxf(0.f, l0 - e1 * (vn + bias) * ik0);
+    float d0 = nl0 - l0;
+    v1 += w01 * d0;
+    v2 += w02 * d0;
+    float lim = mu * nl0;
+    float nl1 = fminf(fmaxf(l1 - v1 * (om * ik1), -lim), lim);
+    float d1 = nl1 - l1;
+    v2 += w12 * d1;
+    float nl2 = fminf(fmaxf(l2 - v2 * (om * ik2), -lim), lim);
+    float d2 = nl2 - l2;
+    const float Px = d0 * n.x + d1 * t1.x + d2 * t2.x;
+    const float Py = d0 * n.y + d1 * t1.y + d2 * t2.y;
+    const float Pz = d0 * n.z + d1 * t1.z + d2 * t2.z;
+    const float2 PX = bc2(Px), PY = bc2(Py), PZ = bc2(Pz);
+    // v += (-ima, imb) P;  w += (-Ia, Ib) (r x P)
+    vx = __ffma2_rn(im, PX, vx);
+    vy = __ffma2_rn(im, PY, vy);
+    vz = __ffma2_rn(im, PZ, vz);
+    const float2 cx = __ffma2_rn(ry, PZ, __fmul2_rn(nrz, PY));
+    const float2 cy = __ffma2_rn(rz, PX, __fmul2_rn(nrx, PZ));
+    const float2 cz = __ffma2_rn(rx, PY, __fmul2_rn(nry, PX));
+    wx = __ffma2_rn(Ixx, cx, __ffma2_rn(Ixy, cy, __ffma2_rn(Ixz, cz, wx)));
+    wy = __ffma2_rn(Ixy, cx, __ffma2_rn(Iyy, cy, __ffma2_rn(Iyz, cz, wy)));
+    wz = __ffma2_rn(Ixz, cx, __ffma2_rn(Iyz, cy, __ffma2_rn(Izz, cz, wz)));
+    VSP(10, k) = nl0; VSP(11, k) = nl1; VSP(12, k) = nl2;
+  }
+  if (da) { VF(FV, a) = vx.x; VF(FV + 1, a) = vy.x; VF(FV + 2, a) = vz.x;
+            VF(FW, a) = wx.x; VF(FW + 1, a) = wy.x; VF(FW + 2, a) = wz.x; }
+  if (db) { VF(FV, b) = vx.y; VF(FV + 1, b) = vy.y; VF(FV + 2, b) = vz.y;
+            VF(FW, b) = wx.y; VF(FW + 1, b) = wy.y; VF(FW + 2, b) = wz.y; }
+}
+
 // Residual of one pair at the current state (no update): max over rows of
 // k |proj(lambda - (v + b) / k) - lambda|, k the inverse effective mass.  It
 // only feeds the stopping test and the statistics, so the division by the
@@ -659,7 +746,10 @@ __device__ __noinline__ void colour_passes_t(const SolverRef r, const int* __res
         else for (int sl = s0; sl < s1; ++sl) pair_pass<mode>(V, sl, e1, om, beta, slop);
       }
     } else {
-      for (int sl = s0 + lane; sl < s1; sl += 32) pair_pass<mode>(V, sl, e1, om, beta, slop);
+      for (int sl = s0 + lane; sl < s1; sl += 32) {
+        if constexpr (mode == 1) pair_sweep_packed(V, sl, e1, om);
+        else pair_pass<mode>(V, sl, e1, om, beta, slop);
+      }
     }
     __syncwarp();
   }
@@ -1104,7 +1194,6 @@ __device__ StepOut substep(const Dev& D, const Ep& E, EpState& st, float h) {
       W(3, 1.f / w00); W(4, 1.f / w11); W(5, 1.f / w22);
       W(6, w01); W(7, w02); W(8, w12); W(9, bias);
       W(10, q[7]); W(11, q[8]); W(12, q[9]);
-#undef W
       if (want_features) {
         // warm-start features: pre-solve relative velocity in the contact
         // frame, depth, frame, inverse masses, body inertias, mu, previous
@@ -1122,6 +1211,12 @@ __device__ StepOut substep(const Dev& D, const Ep& E, EpState& st, float h) {
         f[22] = q[10]; f[23] = a < 0 ? 1.f : 0.f;
       }
     }
+    // unused point records of the pair: zero inverse mass and impulses, so
+    // that the sweep can run all kMaxPts points without a branch (a zero
+    // record's impulse change is exactly zero)
+    for (int k = np; k < kMaxPts; ++k)
+      for (int f = 0; f < kSrtPtFloats; ++f) W(f, 0.f);
+#undef W
   }
   __syncwarp();
 
