@@ -62,8 +62,9 @@ def parse():
                     help="fixed-sweep mode with this many sweeps per solve (profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="friction", choices=["friction", "ragged"],
-                    help="friction: 450 x 18-level towers (the headline); ragged: 4096 towers of 6-30 levels")
+    ap.add_argument("--workload", default="friction", choices=["friction", "ragged", "stress"],
+                    help="friction: 450 x 18-level towers (the headline); ragged: 4096 towers of 6-30 levels; "
+                         "stress: 48-level towers (152 of the 16384 unless --episodes)")
     ap.add_argument("--autotune", action="store_true", help="pick smem_pair_factor and the residual-check cadence by trials")
     ap.add_argument("--warm-start", default="learned", choices=["learned", "plain"],
                     help="learned: train the warm-start network first and keep it if the gate passes")
@@ -79,11 +80,23 @@ def parse():
 def make_workload(kind, seed):
     if kind == "ragged":
         return synth.ragged_workload(seed=seed)
+    if kind == "stress":
+        return synth.stress_workload(seed=seed)
     return synth.friction_workload(seed=seed)
 
 
+WORKLOAD_SEED = {"friction": 1, "ragged": 2, "stress": 5}
+WORKLOAD_NAME = {"friction": "450 episodes x 18-level towers, mu {0.25,0.40,0.60} x 150, removal rounds",
+                 "ragged": "4096 episodes, levels U{6..30}, mu U[0.2,0.7], removal rounds",
+                 "stress": "48-level towers, mu cycling {0.25,0.40,0.60}, one X push at 2x threshold "
+                           "on a level in 10..30, 720 steps"}
+
+
 def workload(args, rank):
-    scene, prot, prm = make_workload(getattr(args, "workload", "friction"), (2 if getattr(args, "workload", "friction") == "ragged" else 1) + rank)
+    kind = getattr(args, "workload", "friction")
+    scene, prot, prm = make_workload(kind, WORKLOAD_SEED[kind] + rank)
+    if kind == "stress" and not args.episodes:
+        args.episodes = 152     # one 48-level episode per SM of the 16384
     if args.episodes:
         # spread the subset over the three friction levels
         E = scene.n_episodes
@@ -109,6 +122,22 @@ def reduce_ranks(times_ms, walls_s, body_steps, device, dist=None):
 
 
 MLP_FLOP = 2.0 * (24 * 128 + 128 * 128 + 128 * 3)   # per predicted contact point
+
+# DRAM bytes (read + write) of one full-job episode_kernel launch, from
+# `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none
+#  -k regex:episode_kernel -s 3 -c 1 python bench.py --warm-start plain --no-cpu`
+# (1 pass): 10.88 MB read + 276.30 MB written.  Valid only for the kernel
+# sources it was taken on; any change to them reports null.
+TRAFFIC = {"bytes": 10.88e6 + 276.30e6, "workload": "friction", "sources_sha1": "292c4d6cae6c52d544f494f53f4229a3ec94434c"}
+
+
+def kernel_sources_sha1():
+    import hashlib
+    h = hashlib.sha1()
+    for f in ("jb_kernels.cu", "jb_internal.cuh", "jb_mlp.cuh"):
+        with open(os.path.join(ROOT, "paper_2606_28394_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 
 
 def prepare_learned(args, rank, prm, device):
@@ -343,7 +372,10 @@ def main():
     peak_tf = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12
     achieved = flops / (ms / args.steps / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
-            "frac": achieved / peak_tf, "traffic": None,
+            "frac": achieved / peak_tf,
+            "traffic": (TRAFFIC["bytes"] if (TRAFFIC["sources_sha1"] == kernel_sources_sha1()
+                                             and args.workload == TRAFFIC["workload"] and not args.episodes
+                                             and not args.fixed_iters) else None),
             "mlp_flops_per_launch": mlp_flops,
             "mlp_roofline_ms": mlp_flops / (float(peaks.get("bf16_tflops", 1892.9)) * 1e12) * 1e3,
             "peak_note": f"FP32 FMA peak: {SMS} SMs x {FP32_LANES} lanes x 2 flop x {sm_max:.0f} MHz (max SM clock of measured)",
@@ -353,10 +385,8 @@ def main():
             "value": value, "unit": "body-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": (("450 episodes x 18-level towers, mu {0.25,0.40,0.60} x 150, removal rounds"
-                                     if args.workload == "friction" else
-                                     "4096 episodes, levels U{6..30}, mu U[0.2,0.7], removal rounds")
-                                    if not args.episodes else f"{args.episodes} episodes of the {args.workload} workload")
+            "config": {"workload": (WORKLOAD_NAME[args.workload] if not args.episodes else
+                                    f"{args.episodes} episodes (evenly spaced) of: {WORKLOAD_NAME[args.workload]}")
                                    + (f", fixed {args.fixed_iters} sweeps (profiling)" if args.fixed_iters else ""),
                        "residual_tol": args.tol, "pgs_iter_cap": args.cap, "max_steps": args.max_steps,
                        "residual_check_every": [jb.params_from_dict(run_prm).residual_every,
@@ -373,6 +403,10 @@ def main():
             "e2e": e2e,
             "solver": {"sweeps_per_solve": float(st["total_sweeps"].sum() / max(st["solves"].sum(), 1)),
                        "not_converged_episodes": int(((st["status"] & jb.JB_EP_NOT_CONVERGED) != 0).sum()),
+                       "solves": float(st["solves"].sum()),
+                       "capped_solves": int(st["capped_solves"].sum()),
+                       "capped_fraction": float(st["capped_solves"].sum() / max(st["solves"].sum(), 1)),
+                       "sweeps_share_busiest_over_mean": float(st["total_sweeps"].max() / max(st["total_sweeps"].mean(), 1)),
                        "collapsed": int(st["collapsed"].sum()), "body_steps_per_job": body_steps,
                        "max_colours": int(st["max_colours"].max()),
                        # critical path: job time over the busiest episode's sweeps

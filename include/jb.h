@@ -181,7 +181,7 @@ typedef struct {
   int32_t last_sweeps;
   int32_t steps;
   int32_t max_colours;      /* most colours used by one solve (Gauss-Seidel phases per sweep) */
-  int32_t reserved;
+  int32_t capped_solves;    /* residual mode: solves that reached pgs_iter_cap above the tolerance */
   float com_imbalance;      /* minus the support-polygon margin of Eq. stability, m */
   float kinetic;            /* J, active dynamic bodies */
   float last_residual;      /* m/s */

@@ -77,7 +77,7 @@ class jb_episode_stats(C.Structure):
     _fields_ = [("status", C.c_int32), ("phase", C.c_int32), ("collapsed", C.c_int32),
                 ("resting", C.c_int32), ("n_fallen", C.c_int32), ("moves_done", C.c_int32),
                 ("n_pairs", C.c_int32), ("n_points", C.c_int32), ("last_sweeps", C.c_int32),
-                ("steps", C.c_int32), ("max_colours", C.c_int32), ("reserved", C.c_int32),
+                ("steps", C.c_int32), ("max_colours", C.c_int32), ("capped_solves", C.c_int32),
                 ("com_imbalance", C.c_float), ("kinetic", C.c_float),
                 ("last_residual", C.c_float), ("max_residual", C.c_float),
                 ("total_sweeps", C.c_double), ("solves", C.c_double),

@@ -41,7 +41,7 @@ struct EpState {
   int32_t phase, mi, remaining, pb, rest_left;
   int32_t collapsed, resting, status;
   int32_t cur, npairs, ncolours, npoints;
-  int32_t last_sweeps, steps, n_fallen, max_colours;
+  int32_t last_sweeps, steps, n_fallen, max_colours, capped;
   float last_res, max_res, kinetic, com_imb;
   double total_sweeps, solves, body_steps;
   double point_sweeps, point_steps, pair_steps, bp_tests, mlp_points;

@@ -1468,6 +1468,7 @@ __device__ void run_episode(const Dev& D, int e, int mode, int max_steps, unsign
       st.solves += 1.0;
       st.npoints = o.npoints;
       st.max_colours = max(st.max_colours, o.ncol);
+      st.capped += (o.status & JB_EP_NOT_CONVERGED) ? 1 : 0;
       st.point_sweeps += (double)o.npoints * o.sweeps;
       st.point_steps += o.npoints;
       st.pair_steps += o.npairs;
@@ -1794,7 +1795,7 @@ __global__ void stats_kernel(Dev D, jb_episode_stats* out) {
   o.last_sweeps = st.last_sweeps;
   o.steps = st.steps;
   o.max_colours = st.max_colours;
-  o.reserved = 0;
+  o.capped_solves = st.capped;
   o.com_imbalance = imb;
   o.kinetic = ek;
   o.last_residual = st.last_res;

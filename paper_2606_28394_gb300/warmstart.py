@@ -163,3 +163,22 @@ def evaluate(scene, prot, params, net, mode=2, max_steps=1 << 30, device="cuda")
     out["gain"] = out["plain"]["sweeps_per_solve"] / max(out["learned"]["sweeps_per_solve"], 1e-9)
     out["keep"] = out["gain"] > 1.0
     return out
+
+
+def cold_start_gain(scene, params, net, steps=20, mode=2, device="cuda"):
+    """Sweeps per solve on contacts with no previous impulse: the warm-start
+    cache is cleared before every step, so every point is unmatched.  Plain
+    PGS starts those points from zero impulses, the learned warm start from
+    the network's prediction; both solve to the same residual.  Returns
+    (plain, learned, plain / learned)."""
+    out = {}
+    for name, ws in (("plain", 1), ("learned", mode)):
+        b = Batch(scene, dict(params, warm_start=ws), device=device)
+        if ws >= 2:
+            check(jb_set_warmstart_mlp(b.h, net.block.data_ptr()), "jb_set_warmstart_mlp")
+        for _ in range(steps):
+            b.write_state(clear_cache=True)
+            b.step(1)
+        st = b.stats()
+        out[name] = float(st["total_sweeps"].sum() / max(st["solves"].sum(), 1))
+    return out["plain"], out["learned"], out["plain"] / max(out["learned"], 1e-9)

@@ -116,12 +116,18 @@ SCENES = {
     "tower18_perturbed": lambda: synth.perturbed(synth.build_scene([synth.Tower()], 0), 3, dx=3e-4, dang=0.02),
     "pile": lambda: synth.pile_scene(28, seed=5),
     "pile2": lambda: synth.pile_scene(40, seed=11, spread=0.12),
+    # 48 levels (the full-collapse stress towers): 144 bodies, ~530 pairs; a
+    # jitter seed whose SAT decisions are all clear of ties
+    "tower48_perturbed": lambda: synth.perturbed(synth.build_scene([synth.Tower(levels=48)], 0), 9,
+                                                 dx=3e-4, dang=0.02),
 }
 
 
 @pytest.mark.parametrize("name", sorted(SCENES))
 def test_contact_sets_match_oracle(cuda_device, name):
     scene = SCENES[name]()
+    if name == "tower48_perturbed":
+        assert oracle.sat_decisions_clear(scene)
     prm = synth.params(pgs_iters=1)
     b, w = step_both(scene, prm)
     g, o = gpu_contacts(b, 0), oracle_contacts(w, 0)
@@ -146,9 +152,12 @@ def velocity_error(scene, v1, w1, v2, w2):
     return np.max(np.abs(v1 - v2)), np.max(np.abs(w1 - w2).max(0) * diag)
 
 
-@pytest.mark.parametrize("name,tol", [("tower4_perturbed", 1e-6), ("pile", 1e-6), ("tower18", 1e-6)])
+@pytest.mark.parametrize("name,tol", [("tower4_perturbed", 1e-6), ("pile", 1e-6), ("tower18", 1e-6),
+                                      ("tower24", 1e-6)])
 def test_one_step_converged_parity(cuda_device, name, tol):
-    if name == "tower4_perturbed":
+    if name == "tower24":
+        scene = synth.build_scene([synth.Tower(levels=24)], 0)
+    elif name == "tower4_perturbed":
         scene = synth.perturbed(synth.build_scene([synth.Tower(levels=4, mu=0.5)], 1), 5, dx=2e-4, dang=0.01)
     elif name == "pile":
         scene = synth.pile_scene(28, seed=5)
@@ -299,3 +308,17 @@ def test_bad_relaxation_is_refused(cuda_device):
     for bad in (dict(sor=2.0), dict(sor=-0.5), dict(sweep_order=2)):
         with pytest.raises(jb().JBError):
             jb().Batch(scene, synth.params(**bad))
+
+
+def test_capped_solves_are_counted(cuda_device):
+    """A tolerance no solve can reach: every solve ends at the cap and is
+    counted, and the episode carries the not-converged flag."""
+    scene = synth.perturbed(synth.build_scene([synth.Tower(levels=3)], 1), 2, dx=2e-4, dang=0.01)
+    b = jb().Batch(scene, synth.params(residual_tol=1e-12, pgs_iter_cap=40))
+    b.step(3)
+    st = b.stats()
+    assert st["capped_solves"][0] == 3 and st["solves"][0] == 3
+    assert st["status"][0] & jb().JB_EP_NOT_CONVERGED
+    ok = jb().Batch(scene, synth.params(residual_tol=1e-5, pgs_iter_cap=200000))
+    ok.step(3)
+    assert ok.stats()["capped_solves"][0] == 0
