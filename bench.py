@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--workload", default="friction", choices=["friction", "ragged", "stress"],
                     help="friction: 450 x 18-level towers (the headline); ragged: 4096 towers of 6-30 levels; "
                          "stress: 48-level towers (152 of the 16384 unless --episodes)")
+    ap.add_argument("--stall-window", type=int, default=0,
+                    help="residual mode: stop a solve whose residual trend over this many sweeps cannot reach "
+                         "the tolerance within the cap (0 = run every solve to the tolerance or the cap)")
     ap.add_argument("--autotune", action="store_true", help="pick smem_pair_factor and the residual-check cadence by trials")
     ap.add_argument("--warm-start", default="learned", choices=["learned", "plain"],
                     help="learned: train the warm-start network first and keep it if the gate passes")
@@ -102,7 +105,7 @@ def workload(args, rank):
         E = scene.n_episodes
         idx = np.linspace(0, E - 1, args.episodes).round().astype(int)
         scene, prot = synth.subset(scene, prot, idx)
-    prm = dict(prm, residual_tol=args.tol, pgs_iter_cap=args.cap)
+    prm = dict(prm, residual_tol=args.tol, pgs_iter_cap=args.cap, stall_window=getattr(args, "stall_window", 0))
     if args.fixed_iters:
         prm = dict(prm, residual_tol=0.0, pgs_iters=args.fixed_iters)
     return scene, prot, prm
@@ -389,6 +392,7 @@ def main():
                                     f"{args.episodes} episodes (evenly spaced) of: {WORKLOAD_NAME[args.workload]}")
                                    + (f", fixed {args.fixed_iters} sweeps (profiling)" if args.fixed_iters else ""),
                        "residual_tol": args.tol, "pgs_iter_cap": args.cap, "max_steps": args.max_steps,
+                       "stall_window": jb.params_from_dict(run_prm).stall_window,
                        "residual_check_every": [jb.params_from_dict(run_prm).residual_every,
                                                 jb.params_from_dict(run_prm).residual_every_max],
                        "l2": "flushed (256 MB write) before every timed step",

@@ -111,6 +111,12 @@ typedef struct {
                                decay), clamped to [residual_every, residual_every_max]; a solve
                                only ends at a check, so this bounds the extra sweeps a
                                converged solve runs.  0 = residual_every (fixed cadence). */
+  int32_t stall_window;     /* residual mode, 0 = off: every stall_window sweeps the solve fits
+                               the residual's geometric decay over that window and stops when
+                               the fit says the tolerance cannot be reached within
+                               pgs_iter_cap (no decay, or more sweeps needed than are left).
+                               Such a solve counts as capped (JB_EP_NOT_CONVERGED) like one
+                               that runs to the cap. */
 } jb_solver_params;
 
 /* Initial scene: host arrays, B = body_off[n_episodes] bodies. */

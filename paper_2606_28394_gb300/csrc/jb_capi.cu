@@ -197,6 +197,7 @@ Params to_params(const jb_solver_params* p) {
   q.sor = p->sor > 0.f ? p->sor : 1.f;
   q.sweep_order = p->sweep_order;
   q.residual_every_max = p->residual_every_max > p->residual_every ? p->residual_every_max : p->residual_every;
+  q.stall_window = p->stall_window;
   return q;
 }
 
@@ -214,6 +215,7 @@ const char* check_params(const jb_solver_params* p) {
   if (!(p->sor >= 0.f && p->sor < 2.f)) return "sor must be in (0, 2) (0 selects 1)";
   if (p->sweep_order < 0 || p->sweep_order > 1) return "sweep_order must be 0 or 1";
   if (p->residual_every_max < 0) return "residual_every_max must be >= 0";
+  if (p->stall_window < 0) return "stall_window must be >= 0";
   return nullptr;
 }
 

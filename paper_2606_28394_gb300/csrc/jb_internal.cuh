@@ -60,6 +60,7 @@ struct Params {
   float sor;        // PGS relaxation factor omega (1 = plain PGS)
   int sweep_order;  // 1: odd sweeps run the colours in reverse
   int residual_every_max;  // >= residual_every
+  int stall_window;        // 0 = off
 };
 
 // One contact buffer (the batch holds two: this step's and the previous one).

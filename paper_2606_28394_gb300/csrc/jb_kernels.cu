@@ -1242,12 +1242,31 @@ __device__ StepOut substep(const Dev& D, const Ep& E, EpState& st, float h) {
     int next = rmode ? Pm.pgs_min_iters : cap;   // sweep count of the next residual check
     float prev_res = -1.f;
     int prev_at = 0;
+    float win_res = -1.f;   // residual at the start of the current stall window
+    int win_at = 0;
+    bool stalled = false;
     while (sweeps < cap) {
       colour_passes<1>(V, s.off, ncol, lane, e1om, om, Pm.sweep_order == 1 && (sweeps & 1), Pm.beta, Pm.slop);
       ++sweeps;
       if (sweeps >= next || sweeps == cap) {
         res = episode_residual(V, npairs, lane);
         if (!rmode || res <= Pm.residual_tol || !(res == res)) break;
+        // stall test: fit res = win_res * exp(rate * sweeps) over the window
+        // and stop when the fit cannot reach the tolerance within the cap
+        if (Pm.stall_window > 0) {
+          if (win_res < 0.f) {
+            win_res = res;
+            win_at = sweeps;
+          } else if (sweeps - win_at >= Pm.stall_window) {
+            const float rate = res < win_res ? __logf(res / win_res) / (float)(sweeps - win_at) : 0.f;
+            if (!(rate < 0.f) || __logf(Pm.residual_tol / res) < rate * (float)(cap - sweeps)) {
+              stalled = true;
+              break;
+            }
+            win_res = res;
+            win_at = sweeps;
+          }
+        }
         // check cadence: half the sweeps that the decay rate between the
         // last two checks predicts are still needed, within [every, every_max]
         int gap = every_max;
@@ -1263,7 +1282,7 @@ __device__ StepOut substep(const Dev& D, const Ep& E, EpState& st, float h) {
         next = sweeps + gap;
       }
     }
-    if (rmode && sweeps >= cap && !(res <= Pm.residual_tol)) out.status |= JB_EP_NOT_CONVERGED;
+    if (rmode && (sweeps >= cap || stalled) && !(res <= Pm.residual_tol)) out.status |= JB_EP_NOT_CONVERGED;
   }
   // final impulses back to the natural arrays (warm-start cache, readback)
   for (int p = lane; p < npairs; p += 32) {

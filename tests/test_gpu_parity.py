@@ -322,3 +322,20 @@ def test_capped_solves_are_counted(cuda_device):
     ok = jb().Batch(scene, synth.params(residual_tol=1e-5, pgs_iter_cap=200000))
     ok.step(3)
     assert ok.stats()["capped_solves"][0] == 0
+
+
+def test_stall_window_stops_hopeless_solves_early(cuda_device):
+    """With a tolerance FP32 cannot reach, the stall test ends each solve
+    long before the cap and counts it as capped; off (0), the solve runs to
+    the cap."""
+    scene = synth.perturbed(synth.build_scene([synth.Tower(levels=3)], 1), 2, dx=2e-4, dang=0.01)
+    prm = synth.params(residual_tol=1e-12, pgs_iter_cap=20000)
+    b = jb().Batch(scene, dict(prm, stall_window=256))
+    b.step(2)
+    st = b.stats()
+    assert st["capped_solves"][0] == 2 and st["last_sweeps"][0] < 20000 // 4
+    off = jb().Batch(scene, prm)
+    off.step(1)
+    assert off.stats()["last_sweeps"][0] == 20000
+    with pytest.raises(jb().JBError):
+        jb().Batch(scene, dict(prm, stall_window=-1))
