@@ -117,6 +117,11 @@ typedef struct {
                                pgs_iter_cap (no decay, or more sweeps needed than are left).
                                Such a solve counts as capped (JB_EP_NOT_CONVERGED) like one
                                that runs to the cap. */
+  int32_t friction_cone;    /* 0: each tangent row clipped to [-mu lambda_n, mu lambda_n] (Eq.
+                               coulomb_pgs, the default); 1: a point's two tangent rows take one
+                               common step 1/k_t, k_t = max(k_t1, k_t2), and are projected
+                               together onto the disc |lambda_t| <= mu lambda_n (the Coulomb cone
+                               of the PGS figure).  The residual uses the same projection. */
 } jb_solver_params;
 
 /* Initial scene: host arrays, B = body_off[n_episodes] bodies. */

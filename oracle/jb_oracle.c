@@ -613,12 +613,45 @@ static void apply_warm_start(or_episode* E) {
 /* One Gauss-Seidel sweep: Eq. lambda_n (restitution factor applied every
    iteration, as in the listing; bias added for speculative points) and
    Eq. coulomb_pgs (box clip with the just-updated normal impulse). */
-static void pgs_sweep(or_episode* E, double e) {
+/* Disc projection of the tangent impulse (Coulomb cone of the PGS figure):
+   (a1, a2) scaled onto |a| <= lim when outside.  Reading: both tangent rows
+   take the same step 1/k_t with k_t = max(k_t1, k_t2), so that a sliding
+   contact's fixed point has the friction impulse opposite to the sliding
+   velocity (with unequal steps it would lean towards the stiffer row). */
+static void disc_project(double a1, double a2, double lim, double* p1, double* p2) {
+  double m = sqrt(a1 * a1 + a2 * a2);
+  double s = m > lim ? lim / m : 1.0;
+  *p1 = a1 * s;
+  *p2 = a2 * s;
+}
+
+static void pgs_sweep(or_episode* E, double e, int cone) {
   for (int c = 0; c < E->np; ++c) {
     or_pair* pr = &E->pairs[c];
     or_body *A = body_ref(E, pr->a), *B = body_ref(E, pr->b);
     const double* dirs[3] = {pr->n, pr->t1, pr->t2};
     for (int i = 0; i < pr->np; ++i) {
+      if (cone) {
+        /* normal row as in Eq. lambda_n, then both tangent rows from the same
+           state, projected together onto the disc of radius mu lambda_n */
+        double vn = rel_vel(A, B, pr->rA[i], pr->rB[i], dirs[0]);
+        double old0 = pr->lam[i][0];
+        double n0 = fmax(0.0, old0 - (1.0 + e) * (vn + pr->bias[i]) / pr->k[i][0]);
+        pr->lam[i][0] = n0;
+        double P0[3] = {(n0 - old0) * dirs[0][0], (n0 - old0) * dirs[0][1], (n0 - old0) * dirs[0][2]};
+        apply_impulse(A, B, pr->rA[i], pr->rB[i], P0);
+        double v1 = rel_vel(A, B, pr->rA[i], pr->rB[i], dirs[1]);
+        double v2 = rel_vel(A, B, pr->rA[i], pr->rB[i], dirs[2]);
+        double o1 = pr->lam[i][1], o2 = pr->lam[i][2], n1, n2;
+        double kt = fmax(pr->k[i][1], pr->k[i][2]);
+        disc_project(o1 - v1 / kt, o2 - v2 / kt, pr->mu * n0, &n1, &n2);
+        pr->lam[i][1] = n1;
+        pr->lam[i][2] = n2;
+        double Pt[3];
+        for (int j = 0; j < 3; ++j) Pt[j] = (n1 - o1) * dirs[1][j] + (n2 - o2) * dirs[2][j];
+        apply_impulse(A, B, pr->rA[i], pr->rB[i], Pt);
+        continue;
+      }
       for (int r = 0; r < 3; ++r) {
         double vrel = rel_vel(A, B, pr->rA[i], pr->rB[i], dirs[r]);
         double old = pr->lam[i][r], nw;
@@ -637,26 +670,36 @@ static void pgs_sweep(or_episode* E, double e) {
 }
 
 /* Reading of the PGS residual (m/s): max over rows of k |P(lambda - (v+b)/k) - lambda|
-   with P the row's projection (normal: [0, inf); tangents: [-mu ln, mu ln]),
-   evaluated at the current state without updating it. */
-static double pgs_residual(or_episode* E) {
+   with P the row's projection (normal: [0, inf); tangents: [-mu ln, mu ln],
+   or with the cone the tangent pair's disc projection), evaluated at the
+   current state without updating it. */
+static double pgs_residual(or_episode* E, int cone) {
   double r = 0;
   for (int c = 0; c < E->np; ++c) {
     or_pair* pr = &E->pairs[c];
     or_body *A = body_ref(E, pr->a), *B = body_ref(E, pr->b);
     const double* dirs[3] = {pr->n, pr->t1, pr->t2};
-    for (int i = 0; i < pr->np; ++i)
+    for (int i = 0; i < pr->np; ++i) {
+      double tp[3] = {0, 0, 0}, kt = 0;
+      if (cone) {
+        double v1 = rel_vel(A, B, pr->rA[i], pr->rB[i], dirs[1]);
+        double v2 = rel_vel(A, B, pr->rA[i], pr->rB[i], dirs[2]);
+        kt = fmax(pr->k[i][1], pr->k[i][2]);
+        disc_project(pr->lam[i][1] - v1 / kt, pr->lam[i][2] - v2 / kt, pr->mu * pr->lam[i][0], &tp[1], &tp[2]);
+      }
       for (int k = 0; k < 3; ++k) {
         double vrel = rel_vel(A, B, pr->rA[i], pr->rB[i], dirs[k]);
         double l = pr->lam[i][k], proj;
         if (k == 0) proj = fmax(0.0, l - (vrel + pr->bias[i]) / pr->k[i][0]);
+        else if (cone) proj = tp[k];
         else {
           double lim = pr->mu * pr->lam[i][0];
           proj = clampd(l - vrel / pr->k[i][k], -lim, lim);
         }
-        double rr = pr->k[i][k] * fabs(proj - l);
+        double rr = (cone && k > 0 ? kt : pr->k[i][k]) * fabs(proj - l);
         if (!(rr <= r)) r = rr;   /* propagates NaN */
       }
+    }
   }
   return r;
 }
@@ -667,19 +710,19 @@ static void solve(or_episode* E, const or_params* P) {
   if (E->np > 0) {
     if (P->residual_tol > 0) {
       for (;;) {
-        pgs_sweep(E, P->restitution);
+        pgs_sweep(E, P->restitution, P->friction_cone);
         ++sweeps;
         if (sweeps >= P->pgs_min_iters) {
-          res = pgs_residual(E);
+          res = pgs_residual(E, P->friction_cone);
           if (res <= P->residual_tol) break;
           if (!(res == res)) break;
         }
         if (sweeps >= P->pgs_iter_cap) { E->status |= OR_STATUS_NOT_CONVERGED; break; }
       }
     } else {
-      for (int s = 0; s < P->pgs_iters; ++s) pgs_sweep(E, P->restitution);
+      for (int s = 0; s < P->pgs_iters; ++s) pgs_sweep(E, P->restitution, P->friction_cone);
       sweeps = P->pgs_iters;
-      res = pgs_residual(E);
+      res = pgs_residual(E, P->friction_cone);
     }
   }
   E->last_sweeps = sweeps;

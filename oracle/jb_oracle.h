@@ -39,6 +39,9 @@ typedef struct {
   double match_radius;   /* warm-start point matching radius (m) */
   double fall_frac, collapse_ek, collapse_theta_deg, rest_ek;
   int rest_steps;
+  int friction_cone;     /* 0: box clip per tangent row (Eq. coulomb_pgs); 1: the two tangent
+                            rows of a point projected together onto the disc |lambda_t| <=
+                            mu lambda_n (the Coulomb cone of the PGS figure) */
 } or_params;
 
 /* episode statistics, one row of OR_NSTAT doubles per episode */

@@ -43,7 +43,8 @@ class jb_solver_params(C.Structure):
                 ("collapse_ek", C.c_float), ("collapse_theta_deg", C.c_float),
                 ("rest_ek", C.c_float), ("rest_steps", C.c_int32),
                 ("smem_pair_factor", C.c_float), ("sor", C.c_float), ("sweep_order", C.c_int32),
-                ("residual_every_max", C.c_int32), ("stall_window", C.c_int32)]
+                ("residual_every_max", C.c_int32), ("stall_window", C.c_int32),
+                ("friction_cone", C.c_int32)]
 
 
 _fp = C.POINTER(C.c_float)

@@ -198,6 +198,7 @@ Params to_params(const jb_solver_params* p) {
   q.sweep_order = p->sweep_order;
   q.residual_every_max = p->residual_every_max > p->residual_every ? p->residual_every_max : p->residual_every;
   q.stall_window = p->stall_window;
+  q.friction_cone = p->friction_cone;
   return q;
 }
 
@@ -216,6 +217,7 @@ const char* check_params(const jb_solver_params* p) {
   if (p->sweep_order < 0 || p->sweep_order > 1) return "sweep_order must be 0 or 1";
   if (p->residual_every_max < 0) return "residual_every_max must be >= 0";
   if (p->stall_window < 0) return "stall_window must be >= 0";
+  if (p->friction_cone < 0 || p->friction_cone > 1) return "friction_cone must be 0 or 1";
   return nullptr;
 }
 

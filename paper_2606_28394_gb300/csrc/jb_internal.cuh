@@ -61,6 +61,7 @@ struct Params {
   int sweep_order;  // 1: odd sweeps run the colours in reverse
   int residual_every_max;  // >= residual_every
   int stall_window;        // 0 = off
+  int friction_cone;       // 1: disc projection of the tangent pair
 };
 
 // One contact buffer (the batch holds two: this step's and the previous one).

@@ -536,6 +536,28 @@ __device__ __forceinline__ void apply_point(PairRegs& R, float3 rA, float3 rB, f
   R.wb = R.wb + mul(R.Ib, cross(rB, P));
 }
 
+// The two tangent rows of a point after its normal row.  Box (Eq.
+// coulomb_pgs): t1 then t2, each clipped to [-lim, lim], t2 seeing t1's
+// change through W_12.  Cone: both rows from the same state with the common
+// step ik_t = min(ik1, ik2) (k_t = max(k_t1, k_t2)), projected together onto
+// the disc of radius lim.
+template <bool kCone>
+__device__ __forceinline__ void tangent_rows(float v1, float v2, float l1, float l2, float ik1, float ik2, float w12,
+                                             float lim, float om, float& nl1, float& nl2) {
+  if constexpr (kCone) {
+    const float ikt = om * fminf(ik1, ik2);
+    const float a1 = l1 - v1 * ikt, a2 = l2 - v2 * ikt;
+    const float m2 = a1 * a1 + a2 * a2;
+    const float sc = m2 > lim * lim ? lim * rsqrtf(m2) : 1.f;
+    nl1 = a1 * sc;
+    nl2 = a2 * sc;
+  } else {
+    nl1 = fminf(fmaxf(l1 - v1 * (om * ik1), -lim), lim);
+    v2 += w12 * (nl1 - l1);
+    nl2 = fminf(fmaxf(l2 - v2 * (om * ik2), -lim), lim);
+  }
+}
+
 // mode 0: apply warm-start impulses; mode 1: one Gauss-Seidel pass over the
 // pair's points, rows n, t1, t2 in order (Eq. lambda_n with the listing's
 // (1+e) factor, Eq. coulomb_pgs box clip with the just-updated normal
@@ -550,7 +572,7 @@ __device__ __forceinline__ void apply_point(PairRegs& R, float3 rA, float3 rB, f
 //
 // Mode 1 relaxes every row by om (projected SOR): the caller folds om into
 // e1 for the normal row; om = 1 is the paper's plain PGS, bit for bit.
-template <int mode, bool kS>
+template <int mode, bool kS, bool kCone = false>
 __device__ __forceinline__ void pair_pass(const SolverView<kS>& V, int sl, float e1, float om, float beta,
                                           float slop) {
   if constexpr (mode == 2) {
@@ -588,10 +610,9 @@ __device__ __forceinline__ void pair_pass(const SolverView<kS>& V, int sl, float
       v1 += w01 * d0;
       v2 += w02 * d0;
       float lim = R.mu * nl0;
-      float nl1 = fminf(fmaxf(l1 - v1 * (om * ik1), -lim), lim);
+      float nl1, nl2;
+      tangent_rows<kCone>(v1, v2, l1, l2, ik1, ik2, w12, lim, om, nl1, nl2);
       float d1 = nl1 - l1;
-      v2 += w12 * d1;
-      float nl2 = fminf(fmaxf(l2 - v2 * (om * ik2), -lim), lim);
       float d2 = nl2 - l2;
       apply_point(R, rA, rB, d0 * R.n + d1 * R.t1 + d2 * R.t2);
       VSP(10, k) = nl0; VSP(11, k) = nl1; VSP(12, k) = nl2;
@@ -610,7 +631,7 @@ __device__ __forceinline__ void pair_pass(const SolverView<kS>& V, int sl, float
 // rounding order.
 __device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
 
-template <bool kS>
+template <bool kS, bool kCone>
 __device__ __forceinline__ void pair_sweep_packed(const SolverView<kS>& V, int sl, float e1, float om) {
   const uint32_t ab = V.ab[sl];
   const int a = ab & 0xffff, b = ab >> 16;
@@ -661,10 +682,9 @@ __device__ __forceinline__ void pair_sweep_packed(const SolverView<kS>& V, int s
     v1 += w01 * d0;
     v2 += w02 * d0;
     float lim = mu * nl0;
-    float nl1 = fminf(fmaxf(l1 - v1 * (om * ik1), -lim), lim);
+    float nl1, nl2;
+    tangent_rows<kCone>(v1, v2, l1, l2, ik1, ik2, w12, lim, om, nl1, nl2);
     float d1 = nl1 - l1;
-    v2 += w12 * d1;
-    float nl2 = fminf(fmaxf(l2 - v2 * (om * ik2), -lim), lim);
     float d2 = nl2 - l2;
     const float Px = d0 * n.x + d1 * t1.x + d2 * t2.x;
     const float Py = d0 * n.y + d1 * t1.y + d2 * t2.y;
@@ -693,7 +713,7 @@ __device__ __forceinline__ void pair_sweep_packed(const SolverView<kS>& V, int s
 // only feeds the stopping test and the statistics, so the division by the
 // stored 1/k is the fast approximate one (a few ulp).
 template <bool kS>
-__device__ __forceinline__ float pair_residual(const SolverView<kS>& V, int sl) {
+__device__ __forceinline__ float pair_residual(const SolverView<kS>& V, int sl, bool cone) {
   PairRegs R;
   load_pair(V, sl, R);
   float r = 0.f;
@@ -706,10 +726,22 @@ __device__ __forceinline__ float pair_residual(const SolverView<kS>& V, int sl) 
     const float l0 = VSP(10, k), l1 = VSP(11, k), l2 = VSP(12, k);
     float lim = R.mu * l0;
     float p0 = fmaxf(0.f, l0 - (dot(u, R.n) + bias) * ik0);
-    float p1 = fminf(fmaxf(l1 - dot(u, R.t1) * ik1, -lim), lim);
-    float p2 = fminf(fmaxf(l2 - dot(u, R.t2) * ik2, -lim), lim);
-    float m = fmaxf(__fdividef(fabsf(p0 - l0), ik0),
-                    fmaxf(__fdividef(fabsf(p1 - l1), ik1), __fdividef(fabsf(p2 - l2), ik2)));
+    float p1, p2, m12;
+    if (cone) {
+      // the tangent pair's disc projection with the common step (see tangent_rows)
+      const float ikt = fminf(ik1, ik2);
+      const float a1 = l1 - dot(u, R.t1) * ikt, a2 = l2 - dot(u, R.t2) * ikt;
+      const float m2 = a1 * a1 + a2 * a2;
+      const float sc = m2 > lim * lim ? lim * rsqrtf(m2) : 1.f;
+      p1 = a1 * sc;
+      p2 = a2 * sc;
+      m12 = __fdividef(fmaxf(fabsf(p1 - l1), fabsf(p2 - l2)), ikt);
+    } else {
+      p1 = fminf(fmaxf(l1 - dot(u, R.t1) * ik1, -lim), lim);
+      p2 = fminf(fmaxf(l2 - dot(u, R.t2) * ik2, -lim), lim);
+      m12 = fmaxf(__fdividef(fabsf(p1 - l1), ik1), __fdividef(fabsf(p2 - l2), ik2));
+    }
+    float m = fmaxf(__fdividef(fabsf(p0 - l0), ik0), m12);
     if (!(m <= r)) r = m;   // keeps NaN
   }
   return r;
@@ -719,11 +751,11 @@ __device__ __forceinline__ float pair_residual(const SolverView<kS>& V, int sl) 
 
 // Residual of the whole episode (warp max; NaN propagates).
 template <bool kS>
-__device__ __noinline__ float episode_residual_t(const SolverRef r, int npairs, int lane) {
+__device__ __noinline__ float episode_residual_t(const SolverRef r, int npairs, int lane, bool cone) {
   const SolverView<kS> V(r);
   float res = 0.f;
   for (int sl = lane; sl < npairs; sl += 32) {
-    float m = pair_residual(V, sl);
+    float m = pair_residual(V, sl, cone);
     if (!(m <= res)) res = m;
   }
   bool nan = __any_sync(FULL, !(res == res));
@@ -733,7 +765,7 @@ __device__ __noinline__ float episode_residual_t(const SolverRef r, int npairs, 
 // Runs `mode` over every colour, in order or (rev) in reverse order; lanes
 // take the slots of a colour.  `off` holds the colour offsets (ncol + 1
 // entries).  Pairs of one colour share no body, so their order is free.
-template <int mode, bool kS>
+template <int mode, bool kS, bool kCone>
 __device__ __noinline__ void colour_passes_t(const SolverRef r, const int* __restrict__ off, int ncol, int lane,
                                              float e1, float om, bool rev, float beta, float slop) {
   const SolverView<kS> V(r);
@@ -742,28 +774,35 @@ __device__ __noinline__ void colour_passes_t(const SolverRef r, const int* __res
     int s0 = off[c], s1 = off[c + 1];
     if (c == kSerial) {
       if (lane == 0) {
-        if (rev) for (int sl = s1 - 1; sl >= s0; --sl) pair_pass<mode>(V, sl, e1, om, beta, slop);
-        else for (int sl = s0; sl < s1; ++sl) pair_pass<mode>(V, sl, e1, om, beta, slop);
+        if (rev) for (int sl = s1 - 1; sl >= s0; --sl) pair_pass<mode, kS, kCone>(V, sl, e1, om, beta, slop);
+        else for (int sl = s0; sl < s1; ++sl) pair_pass<mode, kS, kCone>(V, sl, e1, om, beta, slop);
       }
     } else {
       for (int sl = s0 + lane; sl < s1; sl += 32) {
-        if constexpr (mode == 1) pair_sweep_packed(V, sl, e1, om);
-        else pair_pass<mode>(V, sl, e1, om, beta, slop);
+        if constexpr (mode == 1) pair_sweep_packed<kS, kCone>(V, sl, e1, om);
+        else pair_pass<mode, kS, kCone>(V, sl, e1, om, beta, slop);
       }
     }
     __syncwarp();
   }
 }
 
+// Only the sweep (mode 1) depends on the friction model; the warm start and
+// the position correction run one instantiation.
 template <int mode>
 __device__ __forceinline__ void colour_passes(const SolverRef& r, const int* off, int ncol, int lane, float e1,
-                                              float om, bool rev, float beta, float slop) {
-  if (r.shared) colour_passes_t<mode, true>(r, off, ncol, lane, e1, om, rev, beta, slop);
-  else colour_passes_t<mode, false>(r, off, ncol, lane, e1, om, rev, beta, slop);
+                                              float om, bool rev, float beta, float slop, bool cone = false) {
+  if (mode == 1 && cone) {
+    if (r.shared) colour_passes_t<mode, true, true>(r, off, ncol, lane, e1, om, rev, beta, slop);
+    else colour_passes_t<mode, false, true>(r, off, ncol, lane, e1, om, rev, beta, slop);
+  } else {
+    if (r.shared) colour_passes_t<mode, true, false>(r, off, ncol, lane, e1, om, rev, beta, slop);
+    else colour_passes_t<mode, false, false>(r, off, ncol, lane, e1, om, rev, beta, slop);
+  }
 }
 
-__device__ __forceinline__ float episode_residual(const SolverRef& r, int npairs, int lane) {
-  return r.shared ? episode_residual_t<true>(r, npairs, lane) : episode_residual_t<false>(r, npairs, lane);
+__device__ __forceinline__ float episode_residual(const SolverRef& r, int npairs, int lane, bool cone) {
+  return r.shared ? episode_residual_t<true>(r, npairs, lane, cone) : episode_residual_t<false>(r, npairs, lane, cone);
 }
 
 #undef VF
@@ -775,6 +814,7 @@ __device__ __forceinline__ float episode_residual(const SolverRef& r, int npairs
 // |lambda_t| <= mu lambda_n) as the points' starting impulses.
 __device__ __noinline__ int mlp_warm_start(const Dev& D, const Ep& E, const BufView& Bc, int npairs, bool all_points,
                                            float imp_scale, int lane) {
+  const bool cone = D.P.friction_cone != 0;
   const Sm& s = E.s;
   const MlpLayout L = mlp_layout();
   const float* P = reinterpret_cast<const float*>(D.mlp);
@@ -842,8 +882,16 @@ __device__ __noinline__ int mlp_warm_start(const Dev& D, const Ep& E, const BufV
         float lim = mu * ln;
         float* rec = Bc.sp + sl * kPtStride + k * kSrtPtFloats;
         rec[10] = ln;
-        rec[11] = fminf(fmaxf(stage[lane * 4 + 1] * imp_scale, -lim), lim);
-        rec[12] = fminf(fmaxf(stage[lane * 4 + 2] * imp_scale, -lim), lim);
+        float t1v = stage[lane * 4 + 1] * imp_scale, t2v = stage[lane * 4 + 2] * imp_scale;
+        if (cone) {
+          const float m2 = t1v * t1v + t2v * t2v;
+          const float sc = m2 > lim * lim ? lim * rsqrtf(m2) : 1.f;
+          rec[11] = t1v * sc;
+          rec[12] = t2v * sc;
+        } else {
+          rec[11] = fminf(fmaxf(t1v, -lim), lim);
+          rec[12] = fminf(fmaxf(t2v, -lim), lim);
+        }
       }
       __syncwarp();
     }
@@ -1246,10 +1294,11 @@ __device__ StepOut substep(const Dev& D, const Ep& E, EpState& st, float h) {
     int win_at = 0;
     bool stalled = false;
     while (sweeps < cap) {
-      colour_passes<1>(V, s.off, ncol, lane, e1om, om, Pm.sweep_order == 1 && (sweeps & 1), Pm.beta, Pm.slop);
+      colour_passes<1>(V, s.off, ncol, lane, e1om, om, Pm.sweep_order == 1 && (sweeps & 1), Pm.beta, Pm.slop,
+                       Pm.friction_cone != 0);
       ++sweeps;
       if (sweeps >= next || sweeps == cap) {
-        res = episode_residual(V, npairs, lane);
+        res = episode_residual(V, npairs, lane, Pm.friction_cone != 0);
         if (!rmode || res <= Pm.residual_tol || !(res == res)) break;
         // stall test: fit res = win_res * exp(rate * sweeps) over the window
         // and stop when the fit cannot reach the tolerance within the cap

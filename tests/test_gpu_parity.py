@@ -339,3 +339,54 @@ def test_stall_window_stops_hopeless_solves_early(cuda_device):
     assert off.stats()["last_sweeps"][0] == 20000
     with pytest.raises(jb().JBError):
         jb().Batch(scene, dict(prm, stall_window=-1))
+
+
+def test_cone_friction_sliding_block_fp32(cuda_device):
+    """The cone variant on the GPU: the diagonal slide keeps its direction
+    and loses mu g h of speed per step (FP32)."""
+    sc = synth.custom_scene([dict(half=(0.0375, 0.0125, 0.0075), x=(0, 0, 0.0075), mass=0.015, mu=0.4)],
+                            ground_mu=0.4)
+    sc.v[:, 0] = (0.5 * math.cos(math.radians(30)), 0.5 * math.sin(math.radians(30)), 0.0)
+    b = jb().Batch(sc, synth.params(residual_tol=1e-7, pgs_iter_cap=200000, friction_cone=1))
+    b.step(10)
+    x, q, v, w = b.state()
+    assert abs(math.hypot(v[0, 0], v[1, 0]) - (0.5 - 10 * 0.4 * 9.81 / 240)) < 2e-6
+    assert abs(math.degrees(math.atan2(v[1, 0], v[0, 0])) - 30.0) < 1e-3
+
+
+@pytest.mark.parametrize("name", ["tower4_perturbed", "tower18", "pile"])
+def test_cone_friction_converges_to_the_oracle(cuda_device, name):
+    if name == "tower4_perturbed":
+        scene = synth.perturbed(synth.build_scene([synth.Tower(levels=4, mu=0.5)], 1), 5, dx=2e-4, dang=0.01)
+    elif name == "pile":
+        scene = synth.pile_scene(28, seed=5)
+    else:
+        scene = synth.build_scene([synth.Tower()], 0)
+    prm = synth.params(residual_tol=1e-6, pgs_iter_cap=200000, friction_cone=1)
+    b, w = step_both(scene, prm)
+    st = b.stats()
+    assert st["status"][0] == 0 and st["last_residual"][0] <= 1e-6
+    assert w.stats()["last_residual"][0] <= 1e-6
+    xg, qg, vg, wg = b.state()
+    xo, qo, vo, wo = w.state()
+    assert np.abs(xg - xo).max() < 1e-5
+    if name != "pile":          # the pile's conditioning, as for relaxed sweeps
+        ev, ew = velocity_error(scene, vg, wg, vo, wo)
+        assert ev < 1e-4 and ew < 1e-4, (ev, ew)
+
+
+def test_paper_block_with_three_substeps(cuda_device):
+    """The paper's own configuration (Appendix A): 8.1 x 2.6 x 1.8 cm blocks
+    of 19.6 g and three substeps per step, converged, against the oracle
+    with the same settings."""
+    tower = synth.Tower(levels=6, dims=(0.081, 0.026, 0.018), mass=0.0196, mu=0.4)
+    scene = synth.perturbed(synth.build_scene([tower], 3), 7, dx=2e-4, dang=0.01)
+    assert oracle.sat_decisions_clear(scene)
+    prm = synth.params(residual_tol=1e-6, pgs_iter_cap=200000, n_sub=3)
+    b, w = step_both(scene, prm, n=2)
+    assert (b.stats()["status"] == 0).all()
+    xg, qg, vg, wg = b.state()
+    xo, qo, vo, wo = w.state()
+    assert np.abs(xg - xo).max() < 1e-5
+    ev, ew = velocity_error(scene, vg, wg, vo, wo)
+    assert ev < 1e-4 and ew < 1e-4, (ev, ew)

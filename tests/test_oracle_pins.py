@@ -531,3 +531,32 @@ def test_decision_guard_flags_a_near_tie():
     sc = scene(0.0)
     sc.x[2, 1] = 0.0225 + 1e-3
     assert not oracle.sat_decisions_clear(sc)
+
+
+def _sliding_block(cone, v0=0.5, phi_deg=30.0, mu=0.4, steps=10):
+    hx, hy, hz = 0.0375, 0.0125, 0.0075
+    m = 0.015
+    sc = synth.custom_scene([dict(half=(hx, hy, hz), x=(0, 0, hz), mass=m, mu=mu)], ground_mu=mu)
+    for k in ("half", "x", "q", "v", "w", "mass", "mu", "ground_mu"):
+        setattr(sc, k, getattr(sc, k).astype(float))
+    sc.half[:, 0] = (hx, hy, hz); sc.x[:, 0] = (0, 0, hz); sc.mass[:] = m; sc.mu[:] = mu; sc.ground_mu[:] = mu
+    phi = math.radians(phi_deg)
+    sc.v[:, 0] = (v0 * math.cos(phi), v0 * math.sin(phi), 0.0)
+    W = oracle.World(sc, synth.params(residual_tol=1e-11, pgs_iter_cap=200000, friction_cone=cone))
+    W.step(steps)
+    return W.state()
+
+
+def test_cone_friction_opposes_sliding_velocity():
+    """Coulomb cone (the PGS figure's disc projection): a block sliding on
+    the ground at 30 deg to the tangent axes keeps its direction and loses
+    mu g h of speed per step, exactly; the box clip of Eq. coulomb_pgs turns
+    it towards the diagonal instead."""
+    v0, mu, n = 0.5, 0.4, 10
+    x, q, v, w = _sliding_block(1, v0, 30.0, mu, n)
+    speed = math.hypot(v[0, 0], v[1, 0])
+    assert abs(speed - (v0 - n * mu * 9.81 / 240.0)) < 1e-9
+    assert abs(math.degrees(math.atan2(v[1, 0], v[0, 0])) - 30.0) < 1e-7
+    assert np.abs(w).max() < 1e-9
+    xb, qb, vb, wb = _sliding_block(0, v0, 30.0, mu, n)
+    assert abs(math.degrees(math.atan2(vb[1, 0], vb[0, 0])) - 30.0) > 5.0
