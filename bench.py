@@ -170,6 +170,24 @@ def prepare_learned(args, rank, prm, device):
     return net, info
 
 
+def outcomes(scene, prot, st):
+    """The friction experiment's table (Tab. results) from the batch: per mu,
+    collapsed episodes N_c, mean rounds (moves performed) and the share of
+    moves pushed along block X (Ziglar's torque moves, 4 mu m g)."""
+    mu = np.asarray(scene.ground_mu, float)
+    out = {}
+    for m in sorted(set(np.round(mu, 2))):
+        sel = np.where(np.abs(mu - m) < 5e-3)[0]
+        done = st["moves_done"][sel]
+        axes = [prot.axis[prot.off[e]:prot.off[e] + int(d)] for e, d in zip(sel, done)]
+        n_moves = int(sum(len(a) for a in axes))
+        n_x = int(sum(int((a == synth.AXIS_X).sum()) for a in axes))
+        out[f"{m:.2f}"] = {"episodes": int(len(sel)), "collapsed": int(st["collapsed"][sel].sum()),
+                           "mean_rounds": float(done.mean()) if len(sel) else 0.0,
+                           "torque_move_pct": 100.0 * n_x / max(n_moves, 1)}
+    return out
+
+
 def algorithmic_flops(st):
     return (FLOP_POINT_SWEEP * st["point_sweeps"].sum() + FLOP_POINT_SETUP * st["point_steps"].sum()
             + FLOP_PAIR * st["pair_steps"].sum() + FLOP_BP * st["bp_tests"].sum()
@@ -416,6 +434,7 @@ def main():
                        # critical path: job time over the busiest episode's sweeps
                        "us_per_sweep_busiest_episode": ms / args.steps * 1e3 / float(st["total_sweeps"].max()),
                        "fixed_iters": args.fixed_iters}}
+    line["outcomes"] = outcomes(scene, prot, st)
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args, scene, prot, prm)
     if rank == 0:

@@ -263,6 +263,24 @@ def stress_workload(seed=5, n=16384):
     return build_scene(towers, seed), _protocol(moves, n), params()
 
 
+def subthreshold_workload(seed=11, n=100, levels=6, push_steps=60, settle_steps=120):
+    """n towers, mu ~ U[0.25, 0.6]; one push of the middle block of a level in
+    1..levels-2 along block Y (k = 3) or X (k = 4) at factor ~ U[0.5, 0.9]
+    of the threshold, not removed.  Below the thresholds nothing should
+    slide out or topple."""
+    towers, moves = [], []
+    for e in range(n):
+        mu = 0.25 + 0.35 * float(u01(seed, e, S_MU, 0))
+        towers.append(Tower(levels=levels, mu=np.float32(mu).item()))
+        lev = 1 + int(u01(seed, e, S_LEVEL, 0) * (levels - 2))
+        axis = AXIS_X if u01(seed, e, S_AXIS, 0) < 0.5 else AXIS_Y
+        sign = 1.0 if u01(seed, e, S_SIGN, 0) < 0.5 else -1.0
+        factor = 0.5 + 0.4 * float(u01(seed, e, S_FORCE, 0))
+        k = 3.0 if axis == AXIS_Y else 4.0
+        moves.append([(3 * lev + 1, axis, sign, factor, k, 0, push_steps, settle_steps)])
+    return build_scene(towers, seed), _protocol(moves, n), params(residual_tol=1e-5, pgs_iter_cap=20000)
+
+
 def subset(scene: Scene, prot: Protocol, episodes):
     """Sub-batch of the given episodes (same per-episode inputs)."""
     episodes = list(episodes)

@@ -390,3 +390,26 @@ def test_paper_block_with_three_substeps(cuda_device):
     assert np.abs(xg - xo).max() < 1e-5
     ev, ew = velocity_error(scene, vg, wg, vo, wo)
     assert ev < 1e-4 and ew < 1e-4, (ev, ew)
+
+
+def test_subthreshold_pushes_agree_with_the_oracle(cuda_device):
+    """Whole episodes compared by outcome: 100 12-level towers, one push of
+    a middle block at 0.5-0.9 of its Ziglar threshold (Y: 3 mu m g, X:
+    4 mu m g), then a settle.  Topple/no-topple and the fallen-block count
+    agree on at least 99 %, and the COM imbalance of the standing towers
+    within 1 mm."""
+    scene, prot, prm = synth.subthreshold_workload(levels=12)
+    b = jb().Batch(scene, prm, max_moves=int(prot.off[-1]))
+    b.set_protocol(prot)
+    b.run_protocol()
+    w = oracle.World(as64(scene), prm)
+    w.set_protocol(prot)
+    w.run_protocol()
+    sg, so = b.stats(), w.stats()
+    assert (sg["phase"] == jb().JB_PH_DONE).all() and (so["phase"] == oracle.PH_DONE).all()
+    assert (sg["collapsed"] == so["collapsed"]).mean() >= 0.99
+    assert (sg["n_fallen"] == so["n_fallen"]).mean() >= 0.99
+    standing = (sg["collapsed"] == 0) & (so["collapsed"] == 0)
+    assert standing.mean() >= 0.95
+    d = np.abs(sg["com_imbalance"][standing] - so["com_imbalance"][standing])
+    assert d.max() < 1e-3, d.max()
