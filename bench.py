@@ -332,6 +332,8 @@ def main():
         net, learned = prepare_learned(args, rank, prm, dev)
     run_prm = dict(prm, warm_start=2 if (learned and learned["kept"]) else 1)
 
+    launches = [1]
+
     def job(max_steps, params=None):
         """One pass through the C ABI from host buffers: create the batch
         (scene upload), upload the schedule, run every episode through it in
@@ -345,6 +347,7 @@ def main():
         e1 = torch.cuda.Event(enable_timing=True)
         t0 = time.perf_counter()
         b = jb.Batch(scene, params, max_moves=M, stream=stream, device=dev, workspace=ws)
+        launches[0] = len(b.size_classes())     # episode-kernel launches per run_protocol
         if params["warm_start"] >= 2:
             jb.check(jb.jb_set_warmstart_mlp(b.h, net.block.data_ptr()), "jb_set_warmstart_mlp")
         b.set_protocol(prot)
@@ -384,7 +387,7 @@ def main():
     if not args.no_e2e:
         e2e = {"value": total_body_steps / wall_max, "unit": "body-steps/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "gpu_launches_per_step": 5,
+               "gpu_launches_per_step": 4 + launches[0],
                "note": "host wall clock over jb_batch_create (scene upload from pageable host arrays), "
                        "jb_set_protocol, jb_run_protocol, jb_read_episode_stats"}
 
@@ -421,7 +424,7 @@ def main():
                            "training": learned, "plain_judge": plain,
                            "learned_over_plain": (value / plain["value"]) if plain else None},
             "autotune": tuning,
-            "roofline": roof, "gpu_launches": args.steps, "clocks": clk.summary(),
+            "roofline": roof, "gpu_launches": args.steps * launches[0], "clocks": clk.summary(),
             "e2e": e2e,
             "solver": {"sweeps_per_solve": float(st["total_sweeps"].sum() / max(st["solves"].sum(), 1)),
                        "not_converged_episodes": int(((st["status"] & jb.JB_EP_NOT_CONVERGED) != 0).sum()),

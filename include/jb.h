@@ -256,6 +256,14 @@ jb_status jb_step(jb_batch* b, int32_t n_steps);
 /* Waits for queued work; *n_bad_episodes (may be NULL) = episodes whose status is non-zero. */
 jb_status jb_sync(jb_batch* b, int32_t* n_bad_episodes);
 
+/* Size classes of the batch (episodes split by body count at creation, each
+ * launched as one persistent kernel per jb_step / jb_run_protocol call): the
+ * count and, if the arrays are non-NULL, each class's episode count, largest
+ * body count and grid size (host arrays of at least 4 entries).  No device
+ * work.  (Launch bookkeeping for callers; the paper has no counterpart.) */
+jb_status jb_size_classes(const jb_batch* b, int32_t* n_classes, int32_t* episodes, int32_t* max_bodies,
+                          int32_t* grid);
+
 /* State transfer, [3][B] / [4][B] arrays, host pointers unless device_ptrs != 0
  * (then device pointers, copied on the batch stream).  Any pointer may be NULL.
  * jb_write_state keeps the contact cache unless clear_cache != 0 and, when

@@ -104,6 +104,7 @@ _sig = {
     "jb_remove_block": (C.c_int32, [_vp, C.c_int32, _ip, _ip]),
     "jb_step": (C.c_int32, [_vp, C.c_int32]),
     "jb_sync": (C.c_int32, [_vp, _ip]),
+    "jb_size_classes": (C.c_int32, [_vp, _ip, _ip, _ip, _ip]),
     "jb_read_state": (C.c_int32, [_vp, _vp, _vp, _vp, _vp, C.c_int32]),
     "jb_write_state": (C.c_int32, [_vp, _vp, _vp, _vp, _vp, C.c_int32, C.c_int32, C.c_int32]),
     "jb_read_active": (C.c_int32, [_vp, _ip]),
@@ -260,6 +261,14 @@ class Batch:
     def remove_block(self, episode, block):
         ep, bl = _i32(np.atleast_1d(episode)), _i32(np.atleast_1d(block))
         check(jb_remove_block(self.h, len(ep), _pi(ep), _pi(bl)), "jb_remove_block")
+
+    def size_classes(self):
+        """[(episodes, largest body count, grid)] per size class (one
+        episode-kernel launch each per step or protocol call)."""
+        n = C.c_int32(0)
+        e, nb, g = (np.zeros(4, np.int32) for _ in range(3))
+        check(jb_size_classes(self.h, C.byref(n), _pi(e), _pi(nb), _pi(g)), "jb_size_classes")
+        return [(int(e[i]), int(nb[i]), int(g[i])) for i in range(n.value)]
 
     def sync(self):
         n = C.c_int32(0)

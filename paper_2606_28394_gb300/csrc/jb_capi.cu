@@ -592,6 +592,18 @@ jb_status jb_remove_block(jb_batch* b, int32_t n, const int32_t* ep, const int32
   return JB_OK;
 }
 
+jb_status jb_size_classes(const jb_batch* b, int32_t* n_classes, int32_t* episodes, int32_t* max_bodies,
+                          int32_t* grid) {
+  if (!b || !n_classes) return fail(JB_EINVAL, "jb_size_classes: null argument");
+  *n_classes = (int32_t)b->cls.size();
+  for (size_t c = 0; c < b->cls.size(); ++c) {
+    if (episodes) episodes[c] = b->cls[c].count;
+    if (max_bodies) max_bodies[c] = b->cls[c].nb_max;
+    if (grid) grid[c] = (int32_t)b->cls[c].grid;
+  }
+  return JB_OK;
+}
+
 jb_status jb_sync(jb_batch* b, int32_t* n_bad) {
   if (!b) return fail(JB_EINVAL, "jb_sync: null batch");
   CU(cudaStreamSynchronize(b->stream));

@@ -22,6 +22,8 @@ def test_size_classes_do_not_change_results(cuda_device):
     scene = synth.perturbed(synth.build_scene(towers, 21), 22, dx=1e-4, dang=0.005)
     prm = synth.params(residual_tol=1e-5, pgs_iter_cap=20000)
     b = jb().Batch(scene, prm)
+    # bodies 75, 54, 39 | 27, 18 | 12: a class ends at half its largest tower
+    assert [c[:2] for c in b.size_classes()] == [(3, 75), (2, 27), (1, 12)]
     b.step(6)
     x, q, v, w = b.state()
     st = b.stats()
