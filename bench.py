@@ -71,10 +71,13 @@ def parse():
     ap.add_argument("--autotune", action="store_true", help="pick smem_pair_factor and the residual-check cadence by trials")
     ap.add_argument("--warm-start", default="learned", choices=["learned", "plain"],
                     help="learned: train the warm-start network first and keep it if the gate passes")
-    ap.add_argument("--train-episodes", type=int, default=96)
-    ap.add_argument("--train-steps", type=int, default=480)
-    ap.add_argument("--train-rows", type=int, default=3_000_000)
+    ap.add_argument("--train-episodes", type=int, default=96,
+                    help="learned path: episodes (other seeds) whose converged solves make the training set")
+    ap.add_argument("--collect-steps", type=int, default=1 << 30, help="steps of their schedule to record")
+    ap.add_argument("--collect-every", type=int, default=32, help="record every n-th converged solve")
+    ap.add_argument("--train-rows", type=int, default=5_000_000)
     ap.add_argument("--gate-episodes", type=int, default=48)
+    ap.add_argument("--gate-steps", type=int, default=480)
     ap.add_argument("--cpu-episodes", type=int, default=0)
     ap.add_argument("--cpu-steps", type=int, default=30)
     return ap.parse_args()
@@ -152,18 +155,23 @@ def prepare_learned(args, rank, prm, device):
     t0 = time.perf_counter()
     sc, pr, _ = make_workload(args.workload, 3001 + rank)
     s_tr, p_tr = synth.subset(sc, pr, np.linspace(0, sc.n_episodes - 1, args.train_episodes).round().astype(int))
-    rows = ws.collect(s_tr, p_tr, prm, capacity=args.train_rows, every=2, max_steps=args.train_steps, device=device)
+    rows = ws.collect(s_tr, p_tr, prm, capacity=args.train_rows, every=args.collect_every,
+                      max_steps=args.collect_steps, device=device)
     t1 = time.perf_counter()
     net, hist = ws.train(rows, epochs=30, batch=8192, lr=3e-4, wd=1e-4, device=device)
     torch.cuda.synchronize(device)
     t2 = time.perf_counter()
     sc2, pr2, _ = make_workload(args.workload, 4001 + rank)
     s_ev, p_ev = synth.subset(sc2, pr2, np.linspace(0, sc2.n_episodes - 1, args.gate_episodes).round().astype(int))
-    gate = ws.evaluate(s_ev, p_ev, prm, net, mode=2, max_steps=args.train_steps, device=device)
+    gate = ws.evaluate(s_ev, p_ev, prm, net, mode=2, max_steps=args.gate_steps, device=device)
+    s_cold, _ = synth.subset(sc2, pr2, np.linspace(0, sc2.n_episodes - 1, 10).round().astype(int))
+    cold = ws.cold_start_gain(s_cold, prm, net, steps=12, device=device)
     t3 = time.perf_counter()
     info = {"samples": int(rows.shape[0]), "collect_s": t1 - t0, "train_s": t2 - t1, "gate_s": t3 - t2,
             "epochs": 30, "final_train_loss": hist[-1][1], "final_val_loss": hist[-1][2],
-            "gate": {"episodes": args.gate_episodes, "steps": args.train_steps,
+            "cold_contacts": {"episodes": 10, "steps": 12, "plain_sweeps_per_solve": cold[0],
+                              "learned_sweeps_per_solve": cold[1], "gain": cold[2]},
+            "gate": {"episodes": args.gate_episodes, "steps": args.gate_steps,
                      "plain_sweeps_per_solve": gate["plain"]["sweeps_per_solve"],
                      "learned_sweeps_per_solve": gate["learned"]["sweeps_per_solve"],
                      "gain": gate["gain"]}, "kept": bool(gate["keep"])}

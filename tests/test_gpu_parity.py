@@ -413,3 +413,28 @@ def test_subthreshold_pushes_agree_with_the_oracle(cuda_device):
     assert standing.mean() >= 0.95
     d = np.abs(sg["com_imbalance"][standing] - so["com_imbalance"][standing])
     assert d.max() < 1e-3, d.max()
+
+
+def test_single_push_configuration_matches_the_oracle(cuda_device):
+    """The single-tower configuration: 18 levels, mu 0.40, the middle block
+    of level 9 pushed along Y at 1.05 x 3 mu m g for 0.5 s, 2 s in all, at
+    residual 1e-5.  Converged, the loaded block does not slide (friction
+    from the blocks above exceeds the push); both agree on that, on the
+    outcome and on the final COM imbalance."""
+    scene, prot, prm = synth.single_push_workload()
+    prm = dict(prm, residual_tol=1e-5, pgs_iter_cap=20000)
+    b = jb().Batch(scene, prm, max_moves=int(prot.off[-1]))
+    b.set_protocol(prot)
+    b.run_protocol()
+    w = oracle.World(as64(scene), prm)
+    w.set_protocol(prot)
+    w.run_protocol()
+    sg, so = b.stats(), w.stats()
+    assert sg["steps"][0] == so["steps"][0] == 480
+    assert sg["collapsed"][0] == so["collapsed"][0] == 0 and sg["n_fallen"][0] == so["n_fallen"][0] == 0
+    blk = 8 * 3 + 1
+    xg, xo = b.state()[0], w.state()[0]
+    assert np.abs(xg[:, blk] - scene.x[:, blk]).max() < 2e-5
+    assert np.abs(xo[:, blk] - scene.x[:, blk]).max() < 2e-5
+    assert np.abs(xg - xo).max() < 5e-5
+    assert abs(sg["com_imbalance"][0] - so["com_imbalance"][0]) < 1e-4
