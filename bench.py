@@ -147,7 +147,7 @@ def kernel_sources_sha1():
 
 
 def prepare_learned(args, rank, prm, device):
-    """Trains the warm-start network and gates it (plain PGS is the judge).
+    """Trains the warm-start network and gates it against plain PGS.
     Samples: the plain solver's converged impulses on removal-round towers with
     other seeds than the benchmark (training 3001 + rank, gate 4001 + rank)."""
     from paper_2606_28394_gb300 import warmstart as ws
@@ -383,7 +383,7 @@ def main():
     mlp_flops = MLP_FLOP * float(st["mlp_points"].sum())
     plain = None
     if run_prm["warm_start"] >= 2:
-        # the judge: the same job with plain PGS (previous-frame warm start)
+        # the comparison arm: the same job with plain PGS (previous-frame warm start)
         ms_p, _, st_p = job(args.max_steps, dict(prm, warm_start=1))
         ms_pm, _, bs_p = reduce_ranks(ms_p, 0.0, float(st_p["body_steps"].sum()), dev, dist if world > 1 else None)
         plain = {"value": bs_p / (ms_pm / 1e3), "ms_per_step": ms_pm,
@@ -429,7 +429,7 @@ def main():
                        "episodes": scene.n_episodes, "bodies": scene.n_bodies},
             "warm_start": {"mode": "learned (network on unmatched points, previous-frame elsewhere)"
                            if run_prm["warm_start"] >= 2 else "plain (previous-frame)",
-                           "training": learned, "plain_judge": plain,
+                           "training": learned, "plain_arm": plain,
                            "learned_over_plain": (value / plain["value"]) if plain else None},
             "autotune": tuning,
             "roofline": roof, "gpu_launches": args.steps * launches[0], "clocks": clk.summary(),

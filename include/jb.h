@@ -289,8 +289,8 @@ jb_status jb_save_state(jb_batch* b, void* host_buf, size_t bytes);
 jb_status jb_load_state(jb_batch* b, const void* host_buf, size_t bytes);
 
 /* ---- Learned warm start (not in the paper: a small network that predicts
- * a contact point's starting impulses from local features; plain PGS stays
- * the judge of convergence).
+ * a contact point's starting impulses from local features; plain PGS still
+ * decides convergence, and the gate compares against it).
  *
  * Features (JB_FEATURES floats per contact point, computed after the force
  * predictor and before the solve, with s_v = 1/(|g| h), s_l = 1/(m_bar |g| h),

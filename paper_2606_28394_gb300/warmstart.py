@@ -4,8 +4,9 @@ The network and its training run in the library's kernels (jb_mlp_*): BF16
 tensor-core operands with FP32 accumulation and FP32 master weights.  This
 module only allocates device memory (torch), slices the recorded rows into
 minibatches and drives the calls.  Plain PGS with previous-frame warm start
-is the judge: `evaluate` runs the same episodes with and without the network
-and the gate keeps the network only if it needs fewer sweeps per solve.
+is the yardstick: `evaluate` runs the same episodes with and without the
+network and the gate keeps the network only if it needs fewer sweeps per
+solve.
 """
 from __future__ import annotations
 
