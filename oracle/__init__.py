@@ -75,6 +75,7 @@ def lib():
         L.or_clear_cache.argtypes = [vp]
         L.or_get_contacts.argtypes = [vp, C.c_int, dp, C.c_int]
         L.or_get_stats.argtypes = [vp, dp]
+        L.or_collapse_terms.argtypes = [vp, C.c_int, dp, dp, dp, ip]
         L.or_com_imbalance.argtypes = [vp, C.c_int]
         L.or_com_imbalance.restype = C.c_double
         L.or_active.argtypes = [vp, C.c_int]
@@ -187,6 +188,15 @@ class World:
         out = np.zeros((self.E, NSTAT))
         lib().or_get_stats(self.h, out.ctypes.data_as(C.POINTER(C.c_double)))
         return {name: out[:, i].copy() for i, name in enumerate(STAT_NAMES)}
+
+    def collapse_terms(self, e):
+        """(kinetic J, max displacement / block length, max tilt rad, fallen count)."""
+        ek, dx, th = (np.zeros(1) for _ in range(3))
+        nf = np.zeros(1, np.int32)
+        lib().or_collapse_terms(self.h, e, ek.ctypes.data_as(C.POINTER(C.c_double)),
+                                dx.ctypes.data_as(C.POINTER(C.c_double)), th.ctypes.data_as(C.POINTER(C.c_double)),
+                                nf.ctypes.data_as(C.POINTER(C.c_int)))
+        return float(ek[0]), float(dx[0]), float(th[0]), int(nf[0])
 
     def com_imbalance(self, e):
         return lib().or_com_imbalance(self.h, e)

@@ -1243,6 +1243,10 @@ double or_support_margin(int n, const double* xy, const double* com) {
   return d;
 }
 
+void or_collapse_terms(const or_world* W, int e, double* ek, double* dx_ratio, double* theta, int* n_fallen) {
+  collapse_terms((or_episode*)&W->ep[e], -1, ek, dx_ratio, theta, n_fallen, W->P.fall_frac);
+}
+
 double or_com_imbalance(const or_world* W, int e) {
   const or_episode* E = &W->ep[e];
   const double eps = W->P.aabb_eps;

@@ -89,6 +89,11 @@ long or_recorded(const or_world* W);
 int or_get_contacts(const or_world* W, int episode, double* out, int cap);
 void or_get_stats(or_world* W, double* out);
 double or_com_imbalance(const or_world* W, int episode);
+/* Eq. collapse terms of an episode's current state against its reference
+   poses: kinetic energy (J), largest displacement over block length, largest
+   tilt of a thickness axis (rad), blocks displaced by more than fall_frac. */
+void or_collapse_terms(const or_world* W, int episode, double* ek, double* dx_ratio, double* theta,
+                       int* n_fallen);
 int or_active(const or_world* W, int body);
 
 /* stage-level entry points (pins) */

@@ -438,3 +438,49 @@ def test_single_push_configuration_matches_the_oracle(cuda_device):
     assert np.abs(xo[:, blk] - scene.x[:, blk]).max() < 2e-5
     assert np.abs(xg - xo).max() < 5e-5
     assert abs(sg["com_imbalance"][0] - so["com_imbalance"][0]) < 1e-4
+
+
+def test_speculative_contact_and_baumgarte_closed_forms_fp32(cuda_device):
+    """The oracle's closed-form pins, in FP32 on the GPU: a block 0.5 mm
+    above the ground falling at 1 m/s ends the step exactly touching with
+    v_z = -gap/h; a block sunk 2 mm is raised by beta (depth - slop)."""
+    h, hz, gap, d, beta, slop = 1.0 / 240.0, 0.0075, 5e-4, 2e-3, 0.35, 4e-4
+    prm = synth.params(residual_tol=1e-9, pgs_iter_cap=200000)
+    sc = synth.custom_scene([dict(half=(0.0375, 0.0125, hz), x=(0, 0, hz + gap), mass=0.015)])
+    sc.v[2, 0] = -1.0
+    b = jb().Batch(sc, prm)
+    b.step(1)
+    x, q, v, w = b.state()
+    assert abs(x[2, 0] - hz) < 2e-7 and abs(v[2, 0] + gap / h) < 1e-4
+    sc2 = synth.custom_scene([dict(half=(0.0375, 0.0125, hz), x=(0, 0, hz - d), mass=0.015)])
+    b2 = jb().Batch(sc2, prm)
+    b2.step(1)
+    x2 = b2.state()[0]
+    assert abs(x2[2, 0] - (hz - d + beta * (d - slop))) < 2e-7
+
+
+def test_episode_statistics_on_hand_set_states(cuda_device):
+    """Collapse bookkeeping (Eq. collapse terms, Eq. stability) on states
+    written through the C ABI: kinetic energy, fallen count and COM
+    imbalance against the oracle on the same states."""
+    sc = synth.build_scene([synth.Tower(levels=3, mass_jitter=0.0), synth.Tower(levels=5)], 0)
+    b = jb().Batch(sc, synth.params())
+    w = oracle.World(as64(sc), synth.params())
+    x, q, v, om = (a.astype(np.float64).copy() for a in (sc.x, sc.q, sc.v, sc.w))
+    L = 2 * float(sc.half[0, 4])
+    x[0, 4] += 0.6 * L
+    x[1, 12] -= 0.3 * L
+    ang = math.radians(40.0)
+    c, s = math.cos(ang / 2), math.sin(ang / 2)
+    q0 = q[:, 7].copy()
+    q[:, 7] = [c * q0[0] - s * q0[1], c * q0[1] + s * q0[0], c * q0[2] - s * q0[3], c * q0[3] + s * q0[2]]
+    v[:, 2] = (0.3, 0, 0)
+    om[:, 15] = (0, 0, 2.0)
+    b.write_state(x, q, v, om)
+    w.set_state(x, q, v, om)
+    sg = b.stats()
+    for e in range(2):
+        ek, dxr, th, nf = w.collapse_terms(e)
+        assert sg["n_fallen"][e] == nf
+        assert abs(sg["kinetic"][e] - ek) <= 1e-5 * ek + 1e-12
+        assert abs(sg["com_imbalance"][e] - w.com_imbalance(e)) < 1e-6

@@ -560,3 +560,88 @@ def test_cone_friction_opposes_sliding_velocity():
     assert np.abs(w).max() < 1e-9
     xb, qb, vb, wb = _sliding_block(0, v0, 30.0, mu, n)
     assert abs(math.degrees(math.atan2(vb[1, 0], vb[0, 0])) - 30.0) > 5.0
+
+
+def _one_block(z, vz=0.0, mass=0.015, mu=0.4):
+    hx, hy, hz = 0.0375, 0.0125, 0.0075
+    sc = synth.custom_scene([dict(half=(hx, hy, hz), x=(0, 0, z), mass=mass, mu=mu)], ground_mu=mu)
+    for k in ("half", "x", "q", "v", "w", "mass", "mu", "ground_mu"):
+        setattr(sc, k, getattr(sc, k).astype(float))
+    sc.half[:, 0] = (hx, hy, hz); sc.x[:, 0] = (0, 0, z); sc.mass[:] = mass
+    sc.v[:, 0] = (0, 0, vz)
+    return sc
+
+
+def test_speculative_contact_closes_the_gap_exactly():
+    """Sec. 6 speculative contact: a block 0.5 mm above the ground (inside
+    the 1 mm margin) falling at 1 m/s may only close the gap in one step,
+    so it ends exactly touching with v_z = -gap/h (the row's fixed point is
+    v_n + b = 0 whatever the (1+e) factor).  At 2 mm (outside the margin) it
+    falls freely: v' = v - g h, z' = z + v' h."""
+    h, g, hz = 1.0 / 240.0, 9.81, 0.0075
+    gap = 5e-4
+    W = oracle.World(_one_block(hz + gap, -1.0), synth.params(residual_tol=1e-12, pgs_iter_cap=200000))
+    W.step(1)
+    x, q, v, w = W.state()
+    assert abs(x[2, 0] - hz) < 1e-12 and abs(v[2, 0] + gap / h) < 1e-9
+    W2 = oracle.World(_one_block(hz + 2e-3, -0.1), synth.params(residual_tol=1e-12, pgs_iter_cap=200000))
+    W2.step(1)
+    x2, _, v2, _ = W2.state()
+    assert abs(v2[2, 0] - (-0.1 - g * h)) < 1e-12
+    assert abs(x2[2, 0] - (hz + 2e-3 + (-0.1 - g * h) * h)) < 1e-12
+
+
+def test_baumgarte_correction_closed_form():
+    """Eq. baumgarte (reading: translation only, after the solve): a block
+    sunk 2 mm into the ground, at rest, ends the step raised by
+    beta (depth - slop) along the normal; the velocity solve only cancels
+    gravity.  Two equal dynamic blocks overlapping by 2 mm each move by half
+    of that, apart."""
+    beta, slop, hz, d = 0.35, 4e-4, 0.0075, 2e-3
+    W = oracle.World(_one_block(hz - d), synth.params(residual_tol=1e-12, pgs_iter_cap=200000))
+    W.step(1)
+    x, q, v, w = W.state()
+    assert abs(x[2, 0] - (hz - d + beta * (d - slop))) < 1e-12
+    assert abs(v[2, 0]) < 1e-9
+    hx, hy = 0.0375, 0.0125
+    sc = synth.custom_scene([dict(half=(hx, hy, hz), x=(0, 0, 1.0), mass=0.015, mu=0.4),
+                             dict(half=(hx, hy, hz), x=(0, 0, 1.0 + 2 * hz - d), mass=0.015, mu=0.4)],
+                            ground_mu=0.4)
+    for k in ("half", "x", "q", "v", "w", "mass", "mu", "ground_mu"):
+        setattr(sc, k, getattr(sc, k).astype(float))
+    sc.half[:, :] = np.array([hx, hy, hz])[:, None]; sc.mass[:] = 0.015
+    sc.x[:, 0] = (0, 0, 1.0); sc.x[:, 1] = (0, 0, 1.0 + 2 * hz - d)
+    W2 = oracle.World(sc, synth.params(residual_tol=1e-12, pgs_iter_cap=200000, gravity=(0.0, 0.0, 0.0)))
+    W2.step(1)
+    x2 = W2.state()[0]
+    sep = x2[2, 1] - x2[2, 0]
+    assert abs(sep - (2 * hz - d + beta * (d - slop))) < 1e-12
+    assert abs(x2[2, 0] + x2[2, 1] - (2.0 + 2 * hz - d)) < 1e-12      # symmetric
+
+
+def test_collapse_terms_on_hand_set_states():
+    """Eq. collapse terms against hand values: a block moved by 0.6 of its
+    length counts as fallen (f_d = 0.5) and sets the displacement ratio; a
+    block rotated 40 deg about x sets the tilt; a block moving at v adds
+    m v^2 / 2 of kinetic energy.  The criterion needs all three above their
+    thresholds."""
+    towers = [synth.Tower(levels=3, mass_jitter=0.0)]
+    sc = synth.build_scene(towers, 0)
+    s64 = synth.Scene(sc.body_off, *[getattr(sc, k).astype(np.float64) for k in
+                                     ("half", "mass", "mu", "x", "q", "v", "w", "ground_mu")])
+    W = oracle.World(s64, synth.params())
+    x, q, v, w = (a.copy() for a in W.state())
+    assert W.collapse_terms(0) == (0.0, 0.0, 0.0, 0)
+    L = 2 * s64.half[0, 4]
+    x[0, 4] += 0.6 * L                          # block 4 slid out
+    ang = math.radians(40.0)
+    qr = np.array([math.cos(ang / 2), math.sin(ang / 2), 0, 0])
+    q0 = q[:, 7].copy()                          # block 7 tilted about world x
+    q[:, 7] = [qr[0] * q0[0] - qr[1] * q0[1], qr[0] * q0[1] + qr[1] * q0[0],
+               qr[0] * q0[2] - qr[1] * q0[3], qr[0] * q0[3] + qr[1] * q0[2]]
+    v[:, 2] = (0.3, 0, 0)                        # block 2 moving
+    W.set_state(x, q, v, w)
+    ek, dxr, th, nf = W.collapse_terms(0)
+    assert abs(dxr - 0.6) < 1e-12 and nf == 1
+    assert abs(th - ang) < 1e-9
+    assert abs(ek - 0.5 * s64.mass[2] * 0.09) < 1e-15
