@@ -223,6 +223,24 @@ const char* check_params(const jb_solver_params* p) {
 
 unsigned grid_of(int n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// The episode kernel's dynamic shared-memory limit is a property of the
+// kernel, shared by every batch in the process.  It only ever grows, so a
+// batch created later with smaller towers cannot invalidate the launches of
+// an earlier one.  Per device (the attribute is per context).
+cudaError_t raise_episode_smem_limit(int bytes) {
+  static std::mutex mu;
+  static int limit[64] = {0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  int& cur = limit[dev & 63];
+  if (bytes <= cur) return cudaSuccess;
+  e = cudaFuncSetAttribute(episode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
+}
+
 uint64_t splitmix64(uint64_t x) {
   uint64_t z = x + 0x9E3779B97F4A7C15ull;
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -391,6 +409,10 @@ jb_status jb_batch_create(const jb_scene* sc, const jb_solver_params* p, int32_t
       k.count = j - i;
       k.pc_max = pair_capacity(k.nb_max);
       k.ps = std::min(k.pc_max, (int)(factor * k.nb_max) + 16);
+      // very tall towers: keep fewer pairs on chip (steps with more pairs
+      // solve from the global copy) so that one episode still fits
+      while (k.ps > 0 && kWarpsPerCta * smem_plan(k.nb_max, k.pc_max, k.ps).bytes > smem_max)
+        k.ps = std::max(0, k.ps - 16);
       k.smem = kWarpsPerCta * smem_plan(k.nb_max, k.pc_max, k.ps).bytes;
       smem_all = std::max(smem_all, k.smem);
       bt->cls.push_back(k);
@@ -398,7 +420,7 @@ jb_status jb_batch_create(const jb_scene* sc, const jb_solver_params* p, int32_t
     }
     if (smem_all > smem_max)
       return fin(fail(JB_EINVAL, "towers too large for shared memory (%d > %d bytes)", smem_all, smem_max));
-    CUF(cudaFuncSetAttribute(episode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_all));
+    CUF(raise_episode_smem_limit(smem_all));
     for (auto& k : bt->cls) {
       int oc = 0;
       CUF(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oc, episode_kernel, kWarpsPerCta * 32, k.smem));
@@ -793,7 +815,7 @@ jb_status jb_step_noalloc(int32_t n_episodes, const int32_t* body_off, const flo
   CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   CU(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   if (smem > smem_max) return fail(JB_EINVAL, "towers too large for shared memory (%d > %d bytes)", smem, smem_max);
-  CU(cudaFuncSetAttribute(episode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  CU(raise_episode_smem_limit(smem));
   CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, episode_kernel, kWarpsPerCta * 32, smem));
   if (occ < 1) return fail(JB_EINVAL, "episode kernel cannot be resident with %d bytes of shared memory", smem);
   const unsigned grid = (unsigned)std::max(1, std::min((int)grid_of(z.E, kWarpsPerCta), occ * nsm));

@@ -102,3 +102,33 @@ def test_step_loop_captures_in_a_cuda_graph(cuda_device):
     for u, v in zip(ref.state(), b.state()):
         assert np.array_equal(u, v)
     assert (b.stats()["steps"] == 6).all()
+
+
+def test_global_memory_fallback_matches_shared_memory(cuda_device):
+    """Steps whose pairs exceed the on-chip capacity solve from the global
+    copy of the colour-sorted arrays.  Forcing that path (capacity 0.5 pairs
+    per body) gives the same converged states as the shared-memory path."""
+    scene = synth.perturbed(synth.build_scene([synth.Tower(levels=12)], 8), 9, dx=1e-4, dang=0.005)
+    prm = synth.params(residual_tol=1e-6, pgs_iter_cap=200000)
+    a = jb().Batch(scene, prm)
+    g = jb().Batch(scene, dict(prm, smem_pair_factor=0.5))
+    a.step(3)
+    g.step(3)
+    for u, v in zip(a.state(), g.state()):
+        assert np.abs(u - v).max() < 1e-5
+    assert (g.stats()["status"] & ~jb().JB_EP_NOT_CONVERGED == 0).all()
+
+
+def test_very_tall_tower_fits_by_shrinking_the_on_chip_capacity(cuda_device):
+    """A 100-level tower (300 bodies, ~1,080 pairs) does not fit shared
+    memory at the default capacity; the batch keeps fewer pairs on chip and
+    its steps run from the global copy.  Two steps: no error bits other than
+    the cap, and the flush tower stays put."""
+    scene = synth.build_scene([synth.Tower(levels=100)], 0)
+    b = jb().Batch(scene, synth.params(residual_tol=1e-5, pgs_iter_cap=4000))
+    assert b.size_classes()[0][1] == 300
+    b.step(2)
+    st = b.stats()
+    assert (st["status"] & ~jb().JB_EP_NOT_CONVERGED) == 0
+    x = b.state()[0]
+    assert np.abs(x - scene.x).max() < 1e-3

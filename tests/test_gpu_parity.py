@@ -484,3 +484,26 @@ def test_episode_statistics_on_hand_set_states(cuda_device):
         assert sg["n_fallen"][e] == nf
         assert abs(sg["kinetic"][e] - ek) <= 1e-5 * ek + 1e-12
         assert abs(sg["com_imbalance"][e] - w.com_imbalance(e)) < 1e-6
+
+
+def test_full_friction_batch_sampled_against_the_oracle(cuda_device):
+    """The 450-episode batch in the benchmark's launch configuration (one
+    persistent launch, every episode resident): one converged step from the
+    initial state on the GPU, and six sampled episodes recomputed by the
+    oracle, within the one-step parity bounds."""
+    scene, prot, prm = synth.friction_workload(seed=1)
+    prm = dict(prm, residual_tol=1e-6, pgs_iter_cap=200000)
+    b = jb().Batch(scene, prm)
+    b.step(1)
+    st = b.stats()
+    assert (st["status"] == 0).all() and (st["last_residual"] <= 1e-6).all()
+    x, q, v, w = b.state()
+    sample = [0, 77, 151, 224, 300, 449]
+    sub, _ = synth.subset(scene, prot, sample)
+    o = oracle.World(as64(sub), prm)
+    o.step(1)
+    xo, qo, vo, wo = o.state()
+    idx = np.concatenate([np.arange(scene.body_off[e], scene.body_off[e + 1]) for e in sample])
+    assert np.abs(x[:, idx] - xo).max() < 1e-5
+    ev, ew = velocity_error(sub, v[:, idx], w[:, idx], vo, wo)
+    assert ev < 1e-4 and ew < 1e-4, (ev, ew)
