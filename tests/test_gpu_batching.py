@@ -132,3 +132,29 @@ def test_very_tall_tower_fits_by_shrinking_the_on_chip_capacity(cuda_device):
     assert (st["status"] & ~jb().JB_EP_NOT_CONVERGED) == 0
     x = b.state()[0]
     assert np.abs(x - scene.x).max() < 1e-3
+
+
+def test_empty_episode_and_fully_removed_tower(cuda_device):
+    """Degenerate inputs: an episode with no bodies between two towers, and a
+    tower whose blocks are all removed.  Both step as no-ops (no error bits,
+    no body-steps, COM imbalance 0 as in the oracle), and the other episodes
+    are bit-identical to a batch without them."""
+    prm = synth.params(residual_tol=1e-5, pgs_iter_cap=20000)
+    sc = synth.build_scene([synth.Tower(levels=3), synth.Tower(levels=0), synth.Tower(levels=2)], 0)
+    assert list(sc.body_off) == [0, 9, 9, 15]
+    b = jb().Batch(sc, prm)
+    b.remove_block([2] * 6, list(range(6)))
+    b.step(3)
+    st = b.stats()
+    assert (st["status"] == 0).all()
+    assert st["body_steps"][1] == 0 and st["body_steps"][2] == 0
+    assert st["com_imbalance"][1] == 0
+    w = oracle.World(synth.Scene(sc.body_off, *[getattr(sc, k).astype(np.float64) for k in
+                                                ("half", "mass", "mu", "x", "q", "v", "w", "ground_mu")]), prm)
+    w.step(3)
+    assert w.stats()["com_imbalance"][1] == 0
+    alone = jb().Batch(synth.build_scene([synth.Tower(levels=3)], 0), prm)
+    alone.step(3)
+    for big, small in zip(b.state(), alone.state()):
+        assert np.array_equal(big[:, :9], small)
+    assert not b.active()[9:].any()
