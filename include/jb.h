@@ -122,6 +122,11 @@ typedef struct {
                                common step 1/k_t, k_t = max(k_t1, k_t2), and are projected
                                together onto the disc |lambda_t| <= mu lambda_n (the Coulomb cone
                                of the PGS figure).  The residual uses the same projection. */
+  int32_t restitution_newton; /* 0: the listing's (1+e) factor in every normal row (Sec. 7.1; at
+                               the fixed point v_n = -b, no bounce); 1: Newton restitution, the
+                               rows without the factor and a touching point approaching faster
+                               than restitution_vmin targets v_n = -e v_n(pre-solve) */
+  float restitution_vmin;   /* m/s; <= 0 selects 2 |g| h (resting contacts approach at |g| h) */
 } jb_solver_params;
 
 /* Initial scene: host arrays, B = body_off[n_episodes] bodies. */

@@ -52,7 +52,8 @@ class _Params(C.Structure):
                 ("gravity", C.c_double * 3), ("warm_start", C.c_int),
                 ("match_radius", C.c_double), ("fall_frac", C.c_double),
                 ("collapse_ek", C.c_double), ("collapse_theta_deg", C.c_double),
-                ("rest_ek", C.c_double), ("rest_steps", C.c_int), ("friction_cone", C.c_int)]
+                ("rest_ek", C.c_double), ("rest_steps", C.c_int), ("friction_cone", C.c_int),
+                ("restitution_newton", C.c_int), ("restitution_vmin", C.c_double)]
 
 
 def lib():

@@ -516,9 +516,12 @@ static void detect(or_episode* E, const or_params* P) {
   }
 }
 
+static double rel_vel(const or_body* A, const or_body* B, const double* rA, const double* rB, const double* d);
+
 /* Sec. 7.1 Eq. keff (read as the inverse effective mass) for each row, the
    speculative bias, the tangent basis, and A-local point coordinates. */
-static void setup(or_episode* E, double h) {
+static void setup(or_episode* E, double h, const or_params* P) {
+  const double vmin = P->restitution_vmin > 0 ? P->restitution_vmin : 2.0 * norm3(P->gravity) * h;
   for (int c = 0; c < E->np; ++c) {
     or_pair* pr = &E->pairs[c];
     or_body *A = body_ref(E, pr->a), *B = body_ref(E, pr->b);
@@ -535,8 +538,14 @@ static void setup(or_episode* E, double h) {
         matvec3(A->Iw, ca, ia); matvec3(B->Iw, cb, ib);
         pr->k[i][r] = A->invm + B->invm + dot3(ca, ia) + dot3(cb, ib);
       }
-      /* reading: separated points (depth < 0) may close the gap within the step */
+      /* reading: separated points (depth < 0) may close the gap within the step;
+         with Newton restitution a touching point approaching faster than vmin
+         targets v_n = -e v_n(pre-solve) */
       pr->bias[i] = pr->depth[i] < 0 ? -pr->depth[i] / h : 0.0;
+      if (P->restitution_newton && pr->depth[i] >= 0) {
+        double un = rel_vel(A, B, pr->rA[i], pr->rB[i], pr->n);
+        if (un < -vmin) pr->bias[i] = P->restitution * un;
+      }
       pr->lam[i][0] = pr->lam[i][1] = pr->lam[i][2] = 0;
       pr->matched[i] = 0;
     }
@@ -710,7 +719,7 @@ static void solve(or_episode* E, const or_params* P) {
   if (E->np > 0) {
     if (P->residual_tol > 0) {
       for (;;) {
-        pgs_sweep(E, P->restitution, P->friction_cone);
+        pgs_sweep(E, P->restitution_newton ? 0.0 : P->restitution, P->friction_cone);
         ++sweeps;
         if (sweeps >= P->pgs_min_iters) {
           res = pgs_residual(E, P->friction_cone);
@@ -720,7 +729,7 @@ static void solve(or_episode* E, const or_params* P) {
         if (sweeps >= P->pgs_iter_cap) { E->status |= OR_STATUS_NOT_CONVERGED; break; }
       }
     } else {
-      for (int s = 0; s < P->pgs_iters; ++s) pgs_sweep(E, P->restitution, P->friction_cone);
+      for (int s = 0; s < P->pgs_iters; ++s) pgs_sweep(E, P->restitution_newton ? 0.0 : P->restitution, P->friction_cone);
       sweeps = P->pgs_iters;
       res = pgs_residual(E, P->friction_cone);
     }
@@ -845,7 +854,7 @@ static void substep(or_world* W, or_episode* E, const or_params* P, double h) {
   }
   for (int i = 0; i < E->nb; ++i) update_frame(&E->b[i]);
   detect(E, P);
-  setup(E, h);
+  setup(E, h, P);
   warm_start_match(E, P);
   const int rec = W && W->rec && ((E->solves % W->rec_every) == 0);
   if (rec) features(E, P, h);

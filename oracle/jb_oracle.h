@@ -42,6 +42,11 @@ typedef struct {
   int friction_cone;     /* 0: box clip per tangent row (Eq. coulomb_pgs); 1: the two tangent
                             rows of a point projected together onto the disc |lambda_t| <=
                             mu lambda_n (the Coulomb cone of the PGS figure) */
+  int restitution_newton; /* 0: the listing's (1+e) factor in every normal row (no bounce at
+                            the fixed point); 1: Newton restitution, rows without the factor
+                            and a touching point approaching faster than restitution_vmin
+                            targets v_n = -e v_n(pre-solve) */
+  double restitution_vmin; /* m/s; <= 0 selects 2 |g| h */
 } or_params;
 
 /* episode statistics, one row of OR_NSTAT doubles per episode */

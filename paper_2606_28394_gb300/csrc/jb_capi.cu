@@ -199,6 +199,11 @@ Params to_params(const jb_solver_params* p) {
   q.residual_every_max = p->residual_every_max > p->residual_every ? p->residual_every_max : p->residual_every;
   q.stall_window = p->stall_window;
   q.friction_cone = p->friction_cone;
+  q.restitution_newton = p->restitution_newton;
+  {
+    const float g = sqrtf(p->gravity[0] * p->gravity[0] + p->gravity[1] * p->gravity[1] + p->gravity[2] * p->gravity[2]);
+    q.restitution_vmin = p->restitution_vmin > 0.f ? p->restitution_vmin : 2.f * g * p->dt / (float)p->n_sub;
+  }
   return q;
 }
 
@@ -218,6 +223,7 @@ const char* check_params(const jb_solver_params* p) {
   if (p->residual_every_max < 0) return "residual_every_max must be >= 0";
   if (p->stall_window < 0) return "stall_window must be >= 0";
   if (p->friction_cone < 0 || p->friction_cone > 1) return "friction_cone must be 0 or 1";
+  if (p->restitution_newton < 0 || p->restitution_newton > 1) return "restitution_newton must be 0 or 1";
   return nullptr;
 }
 

@@ -62,6 +62,8 @@ struct Params {
   int residual_every_max;  // >= residual_every
   int stall_window;        // 0 = off
   int friction_cone;       // 1: disc projection of the tangent pair
+  int restitution_newton;  // 1: bounce target instead of the (1+e) factor
+  float restitution_vmin;  // m/s (resolved: > 0)
 };
 
 // One contact buffer (the batch holds two: this step's and the previous one).

@@ -1237,6 +1237,13 @@ __device__ StepOut substep(const Dev& D, const Ep& E, EpState& st, float h) {
       float w12 = dot(ca1, ia2) + dot(cb1, ib2);
       float dep = q[3];
       float bias = dep < 0.f ? -dep * ih : 0.f;
+      if (Pm.restitution_newton && dep >= 0.f) {
+        // Newton restitution: a touching point approaching faster than vmin
+        // targets v_n = -e v_n(pre-solve)
+        const float3 u0 = (s.ld3(FV, b) + cross(s.ld3(FW, b), rB)) - (s.ld3(FV, ia) + cross(s.ld3(FW, ia), rA));
+        const float un = dot(u0, n);
+        if (un < -Pm.restitution_vmin) bias = Pm.restitution * un;
+      }
 #define W(f, v) sp[sl * kPtStride + k * kSrtPtFloats + (f)] = (v)
       W(0, pp.x); W(1, pp.y); W(2, pp.z);
       W(3, 1.f / w00); W(4, 1.f / w11); W(5, 1.f / w22);
@@ -1275,7 +1282,7 @@ __device__ StepOut substep(const Dev& D, const Ep& E, EpState& st, float h) {
 
   // (8) warm start: apply the inherited impulses
   const SolverRef V = solver_ref(s, Bc);
-  const float e1 = 1.f + Pm.restitution;
+  const float e1 = Pm.restitution_newton ? 1.f : 1.f + Pm.restitution;
   if (Pm.warm_start >= 1) colour_passes<0>(V, s.off, ncol, lane, e1, 1.f, false, Pm.beta, Pm.slop);
 
   // (9) projected Gauss-Seidel sweeps

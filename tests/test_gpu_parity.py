@@ -507,3 +507,28 @@ def test_full_friction_batch_sampled_against_the_oracle(cuda_device):
     assert np.abs(x[:, idx] - xo).max() < 1e-5
     ev, ew = velocity_error(sub, v[:, idx], w[:, idx], vo, wo)
     assert ev < 1e-4 and ew < 1e-4, (ev, ew)
+
+
+def test_newton_restitution_fp32_and_parity(cuda_device):
+    """Newton restitution on the GPU: the touching block moving down at
+    1 m/s bounces at e (1 + g h); the default keeps the listing's (1+e)
+    factor and stops it.  A flush 4-level tower landing at 0.3 m/s bounces
+    as one body at e (0.3 + g h), the oracle's state with the same option."""
+    h, e, hz = 1.0 / 240.0, 0.1, 0.0075
+    for newton, expect in ((1, e * (1.0 + 9.81 * h)), (0, 0.0)):
+        sc = synth.custom_scene([dict(half=(0.0375, 0.0125, hz), x=(0, 0, hz), mass=0.015)])
+        sc.v[2, 0] = -1.0
+        b = jb().Batch(sc, synth.params(residual_tol=1e-8, pgs_iter_cap=200000, restitution_newton=newton))
+        b.step(1)
+        assert abs(b.state()[2][2, 0] - expect) < 2e-5, (newton, b.state()[2][2, 0])
+    scene = synth.build_scene([synth.Tower(levels=4, mu=0.5)], 1)
+    scene.v[2, :] = -0.3       # the whole tower lands: only the ground contacts approach
+    prm = synth.params(residual_tol=1e-6, pgs_iter_cap=200000, restitution_newton=1)
+    b, w = step_both(scene, prm)
+    assert b.stats()["status"][0] == 0
+    xg, qg, vg, wg = b.state()
+    xo, qo, vo, wo = w.state()
+    assert np.abs(vg[2] - e * (0.3 + 9.81 * h)).max() < 1e-5
+    assert np.abs(xg - xo).max() < 1e-5
+    ev, ew = velocity_error(scene, vg, wg, vo, wo)
+    assert ev < 1e-4 and ew < 1e-4, (ev, ew)

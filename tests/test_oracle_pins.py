@@ -645,3 +645,22 @@ def test_collapse_terms_on_hand_set_states():
     assert abs(dxr - 0.6) < 1e-12 and nf == 1
     assert abs(th - ang) < 1e-9
     assert abs(ek - 0.5 * s64.mass[2] * 0.09) < 1e-15
+
+
+def test_newton_restitution_bounce_closed_form():
+    """Newton restitution (the paper's Eq. lambda_n with e = 0.1 read as a
+    bounce): a block touching the ground and moving down at 1 m/s leaves
+    the step moving up at e (1 + g h), the pre-solve approach speed times e;
+    with the listing's (1+e) factor (the default) it stops, v_z = 0.  A block
+    resting on the ground (approach g h < 2 g h) does not bounce."""
+    hz, e = 0.0075, 0.1
+    for newton, expect in ((1, e * (1.0 + G * H)), (0, 0.0)):
+        W = one_box_world((0, 0, hz), v=(0, 0, -1.0), residual_tol=1e-12, pgs_iter_cap=200000,
+                          restitution_newton=newton)
+        W.step(1)
+        x, q, v, w = W.state()
+        assert abs(v[2, 0] - expect) < 1e-9, (newton, v[2, 0])
+        assert abs(x[2, 0] - (hz + expect * H)) < 1e-12
+    W = one_box_world((0, 0, hz), residual_tol=1e-12, pgs_iter_cap=200000, restitution_newton=1)
+    W.step(3)
+    assert abs(W.state()[2][2, 0]) < 1e-9
