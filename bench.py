@@ -213,6 +213,21 @@ def outcomes(scene, prot, st):
         out[f"{m:.2f}"] = {"episodes": int(len(sel)), "collapsed": int(st["collapsed"][sel].sum()),
                            "mean_rounds": float(done.mean()) if len(sel) else 0.0,
                            "torque_move_pct": 100.0 * n_x / max(n_moves, 1)}
+    # collapse rate per kind of move (Sec. 13.2's comparison): the moves each
+    # episode attempted (those done plus the one in progress at a collapse),
+    # by slot (centre = 1) and push axis; a collapse is charged to its move
+    kinds = {}
+    for e in range(len(mu)):
+        n_att = int(st["moves_done"][e]) + (1 if st["collapsed"][e] else 0)
+        n_att = min(n_att, int(prot.off[e + 1] - prot.off[e]))
+        for j in range(n_att):
+            mv = int(prot.off[e]) + j
+            slot = int(prot.block[mv]) % 3
+            key = ("centre" if slot == 1 else "side") + ("_x" if int(prot.axis[mv]) == synth.AXIS_X else "_y")
+            kd = kinds.setdefault(key, [0, 0])
+            kd[0] += 1
+            kd[1] += int(bool(st["collapsed"][e]) and j == n_att - 1)
+    out["by_move"] = {k: {"moves": v[0], "collapses": v[1], "rate": v[1] / max(v[0], 1)} for k, v in sorted(kinds.items())}
     return out
 
 
