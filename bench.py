@@ -132,9 +132,9 @@ MLP_FLOP = 2.0 * (24 * 128 + 128 * 128 + 128 * 3)   # per predicted contact poin
 # DRAM bytes (read + write) of one full-job episode_kernel launch, from
 # `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none
 #  -k regex:episode_kernel -s 3 -c 1 python bench.py --warm-start plain --no-cpu`
-# (1 pass): 10.67 MB read + 276.98 MB written.  Valid only for the kernel
+# (1 pass): 11.26 MB read + 270.87 MB written.  Valid only for the kernel
 # sources it was taken on; any change to them reports null.
-TRAFFIC = {"bytes": 10.67e6 + 276.98e6, "workload": "friction", "sources_sha1": "c7f61789759f8543cec8a7b949a5dc2e75d62ffe"}
+TRAFFIC = {"bytes": 11.26e6 + 270.87e6, "workload": "friction", "sources_sha1": "b3f097f64dda6c56cf7f201fc1477a217693c3f0"}
 
 
 def kernel_sources_sha1():
