@@ -166,11 +166,21 @@ def prepare_learned(args, rank, prm, device):
     gate = ws.evaluate(s_ev, p_ev, prm, net, mode=2, max_steps=args.gate_steps, device=device)
     s_cold, _ = synth.subset(sc2, pr2, np.linspace(0, sc2.n_episodes - 1, 10).round().astype(int))
     cold = ws.cold_start_gain(s_cold, prm, net, steps=12, device=device)
+    # short episodes (the first 24 steps of the gate towers, from their cold
+    # start): where contacts without a previous impulse carry much of the work
+    short = ws.evaluate(s_ev, p_ev, prm, net, mode=2, max_steps=24, device=device)
     t3 = time.perf_counter()
     info = {"samples": int(rows.shape[0]), "collect_s": t1 - t0, "train_s": t2 - t1, "gate_s": t3 - t2,
             "epochs": 30, "final_train_loss": hist[-1][1], "final_val_loss": hist[-1][2],
             "cold_contacts": {"episodes": 10, "steps": 12, "plain_sweeps_per_solve": cold[0],
                               "learned_sweeps_per_solve": cold[1], "gain": cold[2]},
+            "short_episodes": {"episodes": args.gate_episodes, "steps": 24,
+                               "plain_body_steps_per_s": short["plain"]["body_steps_per_s"],
+                               "learned_body_steps_per_s": short["learned"]["body_steps_per_s"],
+                               "plain_sweeps_per_solve": short["plain"]["sweeps_per_solve"],
+                               "learned_sweeps_per_solve": short["learned"]["sweeps_per_solve"],
+                               "learned_over_plain": short["learned"]["body_steps_per_s"]
+                               / max(short["plain"]["body_steps_per_s"], 1e-12)},
             "gate": {"episodes": args.gate_episodes, "steps": args.gate_steps,
                      "plain_sweeps_per_solve": gate["plain"]["sweeps_per_solve"],
                      "learned_sweeps_per_solve": gate["learned"]["sweeps_per_solve"],

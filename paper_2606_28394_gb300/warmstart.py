@@ -150,16 +150,22 @@ def evaluate(scene, prot, params, net, mode=2, max_steps=1 << 30, device="cuda")
     """Sweeps per solve and body-steps of the plain solver and of the learned
     warm start (mode 2: unmatched points; 3: all points) on the same episodes,
     and whether the gate keeps the network."""
+    import torch
     out = {}
     for name, ws in (("plain", 1), ("learned", mode)):
         b = Batch(scene, dict(params, warm_start=ws), max_moves=int(prot.off[-1]), device=device)
         if ws >= 2:
             check(jb_set_warmstart_mlp(b.h, net.block.data_ptr()), "jb_set_warmstart_mlp")
         b.set_protocol(prot)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(b.stream)
         b.run_protocol(max_steps)
+        e1.record(b.stream)
         st = b.stats()
+        ms = e0.elapsed_time(e1)
         out[name] = dict(sweeps_per_solve=float(st["total_sweeps"].sum() / max(st["solves"].sum(), 1)),
-                         body_steps=float(st["body_steps"].sum()),
+                         body_steps=float(st["body_steps"].sum()), ms=ms,
+                         body_steps_per_s=float(st["body_steps"].sum()) / max(ms * 1e-3, 1e-12),
                          not_converged=int(((st["status"] & 2) != 0).sum()))
     out["gain"] = out["plain"]["sweeps_per_solve"] / max(out["learned"]["sweeps_per_solve"], 1e-9)
     out["keep"] = out["gain"] > 1.0
