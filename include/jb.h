@@ -55,7 +55,8 @@ typedef int32_t jb_status;
 
 /* per-episode status bits (jb_episode_stats.status) */
 #define JB_EP_CONTACT_OVERFLOW 1  /* more pairs or candidates than the capacity; extras dropped */
-#define JB_EP_NOT_CONVERGED 2     /* residual mode hit pgs_iter_cap at least once */
+#define JB_EP_NOT_CONVERGED 2     /* residual mode: a solve ended above the tolerance (at pgs_iter_cap,
+                                     or stopped by the stall test) at least once */
 #define JB_EP_NONFINITE 4         /* a position or velocity became NaN/Inf; episode stopped */
 #define JB_EP_TOO_MANY_COLOURS 8  /* colouring overflowed; overflow pairs solved serially */
 
