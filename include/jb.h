@@ -288,6 +288,14 @@ jb_status jb_read_contacts(jb_batch* b, int32_t episode, jb_contact* out, int32_
 /* Per-episode statistics [E]; computes the support-polygon margin on the device. */
 jb_status jb_read_episode_stats(jb_batch* b, jb_episode_stats* out);
 
+/* Reference-episode search (Sec. 11.2, the similarity step): among the
+ * collapsed episodes, the one whose count of removed blocks is closest to
+ * n_removed_hat (lowest index on ties); if none collapsed, the one with the
+ * most completed moves (rounds; lowest index on ties).  *episode = the
+ * chosen index, *n_removed (may be NULL) = its removed-block count.
+ * Synchronous: reads the episode statistics and the active flags. */
+jb_status jb_reference_episode(jb_batch* b, int32_t n_removed_hat, int32_t* episode, int32_t* n_removed);
+
 /* Raw snapshot of all mutable device state (bodies, episode state, contact
  * caches, schedule) for exact resume.  jb_state_bytes gives the size. */
 size_t jb_state_bytes(const jb_batch* b);

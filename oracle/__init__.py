@@ -77,6 +77,7 @@ def lib():
         L.or_get_contacts.argtypes = [vp, C.c_int, dp, C.c_int]
         L.or_get_stats.argtypes = [vp, dp]
         L.or_collapse_terms.argtypes = [vp, C.c_int, dp, dp, dp, ip]
+        L.or_reference_episode.argtypes = [vp, C.c_int, ip]
         L.or_com_imbalance.argtypes = [vp, C.c_int]
         L.or_com_imbalance.restype = C.c_double
         L.or_active.argtypes = [vp, C.c_int]
@@ -198,6 +199,11 @@ class World:
                                 dx.ctypes.data_as(C.POINTER(C.c_double)), th.ctypes.data_as(C.POINTER(C.c_double)),
                                 nf.ctypes.data_as(C.POINTER(C.c_int)))
         return float(ek[0]), float(dx[0]), float(th[0]), int(nf[0])
+
+    def reference_episode(self, n_hat):
+        r = np.zeros(1, np.int32)
+        e = lib().or_reference_episode(self.h, int(n_hat), r.ctypes.data_as(C.POINTER(C.c_int)))
+        return int(e), int(r[0])
 
     def com_imbalance(self, e):
         return lib().or_com_imbalance(self.h, e)

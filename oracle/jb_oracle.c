@@ -1256,6 +1256,25 @@ void or_collapse_terms(const or_world* W, int e, double* ek, double* dx_ratio, d
   collapse_terms((or_episode*)&W->ep[e], -1, ek, dx_ratio, theta, n_fallen, W->P.fall_frac);
 }
 
+static int removed_blocks(const or_episode* E) {
+  int r = 0;
+  for (int i = 0; i < E->nb; ++i) r += !E->b[i].active;
+  return r;
+}
+
+int or_reference_episode(const or_world* W, int n_hat, int* n_removed) {
+  int best = -1;
+  for (int e = 0; e < W->E; ++e) {
+    if (!W->ep[e].collapsed) continue;
+    if (best < 0 || abs(removed_blocks(&W->ep[e]) - n_hat) < abs(removed_blocks(&W->ep[best]) - n_hat)) best = e;
+  }
+  if (best < 0)
+    for (int e = 0; e < W->E; ++e)
+      if (best < 0 || W->ep[e].mi > W->ep[best].mi) best = e;
+  if (n_removed) *n_removed = best >= 0 ? removed_blocks(&W->ep[best]) : 0;
+  return best;
+}
+
 double or_com_imbalance(const or_world* W, int e) {
   const or_episode* E = &W->ep[e];
   const double eps = W->P.aabb_eps;

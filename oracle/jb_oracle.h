@@ -94,6 +94,10 @@ long or_recorded(const or_world* W);
 int or_get_contacts(const or_world* W, int episode, double* out, int cap);
 void or_get_stats(or_world* W, double* out);
 double or_com_imbalance(const or_world* W, int episode);
+/* Reference-episode search (Sec. 11.2): argmin over collapsed episodes of
+   |removed blocks - n_hat| (lowest index on ties), else the episode with the
+   most completed moves; returns the index, *n_removed its removed count. */
+int or_reference_episode(const or_world* W, int n_hat, int* n_removed);
 /* Eq. collapse terms of an episode's current state against its reference
    poses: kinetic energy (J), largest displacement over block length, largest
    tilt of a thickness axis (rad), blocks displaced by more than fall_frac. */

@@ -106,6 +106,7 @@ _sig = {
     "jb_step": (C.c_int32, [_vp, C.c_int32]),
     "jb_sync": (C.c_int32, [_vp, _ip]),
     "jb_size_classes": (C.c_int32, [_vp, _ip, _ip, _ip, _ip]),
+    "jb_reference_episode": (C.c_int32, [_vp, C.c_int32, _ip, _ip]),
     "jb_read_state": (C.c_int32, [_vp, _vp, _vp, _vp, _vp, C.c_int32]),
     "jb_write_state": (C.c_int32, [_vp, _vp, _vp, _vp, _vp, C.c_int32, C.c_int32, C.c_int32]),
     "jb_read_active": (C.c_int32, [_vp, _ip]),
@@ -262,6 +263,13 @@ class Batch:
     def remove_block(self, episode, block):
         ep, bl = _i32(np.atleast_1d(episode)), _i32(np.atleast_1d(block))
         check(jb_remove_block(self.h, len(ep), _pi(ep), _pi(bl)), "jb_remove_block")
+
+    def reference_episode(self, n_removed_hat):
+        """(episode, removed blocks): the collapsed episode whose removed-block
+        count is closest to n_removed_hat, else the one with the most rounds."""
+        e, r = C.c_int32(0), C.c_int32(0)
+        check(jb_reference_episode(self.h, int(n_removed_hat), C.byref(e), C.byref(r)), "jb_reference_episode")
+        return e.value, r.value
 
     def size_classes(self):
         """[(episodes, largest body count, grid)] per size class (one

@@ -740,6 +740,32 @@ jb_status jb_read_episode_stats(jb_batch* b, jb_episode_stats* out) {
   return JB_OK;
 }
 
+jb_status jb_reference_episode(jb_batch* b, int32_t n_hat, int32_t* episode, int32_t* n_removed) {
+  if (!b || !episode) return fail(JB_EINVAL, "jb_reference_episode: null argument");
+  std::vector<jb_episode_stats> st(b->E);
+  if (jb_status s = jb_read_episode_stats(b, st.data())) return s;
+  std::vector<int32_t> act(b->B);
+  if (jb_status s = jb_read_active(b, act.data())) return s;
+  int best = -1, best_d = 0, best_r = 0;
+  for (int e = 0; e < b->E; ++e) {
+    if (!st[e].collapsed) continue;
+    int r = 0;
+    for (int i = b->body_off[e]; i < b->body_off[e + 1]; ++i) r += act[i] == 0;
+    const int d = r > n_hat ? r - n_hat : n_hat - r;
+    if (best < 0 || d < best_d) { best = e; best_d = d; best_r = r; }
+  }
+  if (best < 0) {   // nothing collapsed: the episode with the most rounds
+    for (int e = 0; e < b->E; ++e)
+      if (best < 0 || st[e].moves_done > st[best].moves_done) best = e;
+    best_r = 0;
+    if (best >= 0)
+      for (int i = b->body_off[best]; i < b->body_off[best + 1]; ++i) best_r += act[i] == 0;
+  }
+  *episode = best;
+  if (n_removed) *n_removed = best_r;
+  return JB_OK;
+}
+
 size_t jb_state_bytes(const jb_batch* b) { return b ? b->persist_bytes : 0; }
 
 jb_status jb_save_state(jb_batch* b, void* host, size_t bytes) {

@@ -158,3 +158,23 @@ def test_empty_episode_and_fully_removed_tower(cuda_device):
     for big, small in zip(b.state(), alone.state()):
         assert np.array_equal(big[:, :9], small)
     assert not b.active()[9:].any()
+
+
+def test_reference_episode_search(cuda_device):
+    """jb_reference_episode on a batch after removal rounds: the collapsed
+    episode with the removed-block count closest to n_hat (else the most
+    rounds), against the definition over the batch's statistics and active
+    flags."""
+    towers = [synth.Tower(levels=5, mu=m) for m in (0.25, 0.4, 0.6) * 4]
+    sc = synth.build_scene(towers, 21)
+    prot = synth.removal_protocol(towers, 21, push_steps=40, settle_steps=80, max_removals=4)
+    b = jb().Batch(sc, synth.params(pgs_iters=10), max_moves=int(prot.off[-1]))
+    b.set_protocol(prot)
+    b.run_protocol()
+    st, act = b.stats(), b.active()
+    removed = [int((~act[sc.body_off[e]:sc.body_off[e + 1]]).sum()) for e in range(len(towers))]
+    for n_hat in range(6):
+        cand = [e for e in range(len(towers)) if st["collapsed"][e]]
+        want = (min(cand, key=lambda e: (abs(removed[e] - n_hat), e)) if cand
+                else min(range(len(towers)), key=lambda e: (-st["moves_done"][e], e)))
+        assert b.reference_episode(n_hat) == (want, removed[want])

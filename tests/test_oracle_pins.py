@@ -664,3 +664,41 @@ def test_newton_restitution_bounce_closed_form():
     W = one_box_world((0, 0, hz), residual_tol=1e-12, pgs_iter_cap=200000, restitution_newton=1)
     W.step(3)
     assert abs(W.state()[2][2, 0]) < 1e-9
+
+
+def _reference_by_definition(collapsed, removed, moves, n_hat):
+    cand = [e for e in range(len(collapsed)) if collapsed[e]]
+    if cand:
+        return min(cand, key=lambda e: (abs(removed[e] - n_hat), e))
+    return min(range(len(moves)), key=lambda e: (-moves[e], e))
+
+
+def test_reference_episode_search_by_definition():
+    """Sec. 11.2's similarity step on removal rounds of 12 short towers: the
+    collapsed episode with the removed-block count closest to n_hat, else the
+    one with the most rounds (lowest index on ties), against the definition
+    evaluated over the episodes' statistics and active flags."""
+    towers = [synth.Tower(levels=5, mu=m) for m in (0.25, 0.4, 0.6) * 4]
+    sc = synth.build_scene(towers, 21)
+    prot = synth.removal_protocol(towers, 21, push_steps=40, settle_steps=80, max_removals=4)
+    s64 = synth.Scene(sc.body_off, *[getattr(sc, k).astype(np.float64) for k in
+                                     ("half", "mass", "mu", "x", "q", "v", "w", "ground_mu")])
+    W = oracle.World(s64, synth.params(pgs_iters=10))
+    W.set_protocol(prot)
+    W.run_protocol()
+    st, act = W.stats(), W.active()
+    removed = [int((~act[sc.body_off[e]:sc.body_off[e + 1]]).sum()) for e in range(len(towers))]
+    assert st["collapsed"].sum() >= 1
+    for n_hat in range(6):
+        e, r = W.reference_episode(n_hat)
+        assert e == _reference_by_definition(st["collapsed"], removed, st["moves_done"], n_hat)
+        assert r == removed[e]
+    # nothing collapsed: most rounds
+    W2 = oracle.World(s64, synth.params(pgs_iters=10))
+    W2.set_protocol(prot)
+    W2.run_protocol(max_steps=50)
+    st2, act2 = W2.stats(), W2.active()
+    if st2["collapsed"].sum() == 0:
+        removed2 = [int((~act2[sc.body_off[e]:sc.body_off[e + 1]]).sum()) for e in range(len(towers))]
+        assert W2.reference_episode(2)[0] == _reference_by_definition(st2["collapsed"], removed2,
+                                                                       st2["moves_done"], 2)
