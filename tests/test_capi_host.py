@@ -74,3 +74,36 @@ def test_host_argument_errors_need_no_device():
     assert b"null" in jb.jb_last_error()
     h = C.c_void_p()
     assert jb.jb_batch_create(None, C.byref(p), 0, None, 0, None, C.byref(h)) == jb.JB_EINVAL
+
+
+def _c_layouts(structs):
+    """sizeof and field offsets of the header's structs, from gcc."""
+    import subprocess
+    import tempfile
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "jb.h"', "int main(void) {"]
+    for name, fields in structs.items():
+        lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        for f in fields:
+            lines.append(f'  printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["  return 0;", "}"]
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "layout.c"), os.path.join(d, "layout")
+        open(src, "w").write("\n".join(lines))
+        subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), src, "-o", exe])
+        out = subprocess.check_output([exe], text=True)
+    return dict(line.rsplit(" ", 1) for line in out.strip().splitlines())
+
+
+def test_binding_struct_layouts_match_the_header():
+    """Every ctypes mirror of a header struct has the C compiler's size and
+    field offsets (a reordered or missing field would silently corrupt the
+    call)."""
+    import paper_2606_28394_gb300 as jb
+    mirrors = {n: getattr(jb, n) for n in ("jb_solver_params", "jb_scene", "jb_tower_desc", "jb_protocol",
+                                           "jb_contact", "jb_episode_stats")}
+    cname = lambda f: f[:-1] if f.endswith("_") else f     # lambda_ mirrors the C field lambda
+    got = _c_layouts({n: [cname(f) for f, _ in m._fields_] for n, m in mirrors.items()})
+    for n, m in mirrors.items():
+        assert int(got[n]) == C.sizeof(m), n
+        for f, _ in m._fields_:
+            assert int(got[f"{n}.{cname(f)}"]) == getattr(m, f).offset, (n, f)

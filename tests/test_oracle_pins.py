@@ -702,3 +702,24 @@ def test_reference_episode_search_by_definition():
         removed2 = [int((~act2[sc.body_off[e]:sc.body_off[e + 1]]).sum()) for e in range(len(towers))]
         assert W2.reference_episode(2)[0] == _reference_by_definition(st2["collapsed"], removed2,
                                                                        st2["moves_done"], 2)
+
+
+def test_oracle_params_layout_matches_its_header():
+    """The ctypes mirror of or_params has gcc's size and field offsets."""
+    import ctypes as C
+    import subprocess
+    import tempfile
+    fields = [f for f, _ in oracle._Params._fields_]
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "jb_oracle.h"', "int main(void) {",
+             '  printf("size %zu\\n", sizeof(or_params));']
+    lines += [f'  printf("{f} %zu\\n", offsetof(or_params, {f}));' for f in fields]
+    lines += ["  return 0;", "}"]
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "layout.c"), os.path.join(d, "layout")
+        open(src, "w").write("\n".join(lines))
+        subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(root, "oracle"), src, "-o", exe])
+        got = dict(l.rsplit(" ", 1) for l in subprocess.check_output([exe], text=True).strip().splitlines())
+    assert int(got["size"]) == C.sizeof(oracle._Params)
+    for f in fields:
+        assert int(got[f]) == getattr(oracle._Params, f).offset, f
