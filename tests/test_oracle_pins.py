@@ -723,3 +723,21 @@ def test_oracle_params_layout_matches_its_header():
     assert int(got["size"]) == C.sizeof(oracle._Params)
     for f in fields:
         assert int(got[f]) == getattr(oracle._Params, f).offset, f
+
+
+def test_oracle_is_independent_of_thread_count():
+    """Episodes are independent: one thread or several give identical
+    states (no shared scratch between episodes)."""
+    towers = [synth.Tower(levels=3, mu=m) for m in (0.25, 0.4, 0.6, 0.5)]
+    sc = synth.build_scene(towers, 4)
+    prot = synth.removal_protocol(towers, 4, push_steps=10, settle_steps=10, max_removals=2)
+    s64 = synth.Scene(sc.body_off, *[getattr(sc, k).astype(np.float64) for k in
+                                     ("half", "mass", "mu", "x", "q", "v", "w", "ground_mu")])
+    out = []
+    for threads in (1, 4):
+        W = oracle.World(s64, synth.params(residual_tol=1e-6, pgs_iter_cap=20000))
+        W.set_protocol(prot)
+        W.run_protocol(max_steps=40, threads=threads)
+        out.append(W.state())
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
