@@ -92,3 +92,34 @@ def test_recorder_features_of_a_resting_block():
     for r, prev in zip(rows[4:], rows[:4]):   # second step: matched, previous impulses
         assert r[22] == 1
     assert abs(rows[4:, 19].sum() - m / 0.015) < 1e-9
+
+
+def test_warm_start_match_radius():
+    """Warm-start matching (same pair and features, nearest old point within
+    2 mm in body-A coordinates): a block on a static block of the same size
+    keeps its four points' impulses when slid 1 mm along its length between
+    steps.  Slid 3 mm, the two corners on the static block's far edge stay
+    put and match; the two that moved with the top block's end do not, and
+    start from zero (the recorder's matched flag and previous impulses)."""
+    hx, hy, hz = 0.0375, 0.0125, 0.0075
+    for shift, n_matched in ((1e-3, 4), (3e-3, 2)):
+        sc = synth.custom_scene([dict(half=(hx, hy, hz), x=(0, 0, hz), mass=0.0, mu=0.4),
+                                 dict(half=(hx, hy, hz), x=(0, 0, 3 * hz), mass=0.015, mu=0.4)], ground_mu=0.4)
+        for k in ("half", "x", "q", "v", "w", "mass", "mu", "ground_mu"):
+            setattr(sc, k, getattr(sc, k).astype(float))
+        sc.half[:, :] = np.array([hx, hy, hz])[:, None]
+        sc.x[:, 0] = (0, 0, hz); sc.x[:, 1] = (0, 0, 3 * hz); sc.mass[:] = (0.0, 0.015)
+        W = oracle.World(sc, synth.params(residual_tol=1e-10, pgs_iter_cap=20000))
+        W.set_recorder(64, 1)
+        W.step(1)
+        x, q, v, w = W.state()
+        x = x.copy(); x[0, 1] += shift         # slide the top block along its length
+        W.set_state(x, q, np.zeros_like(v), np.zeros_like(w))
+        W.step(1)
+        rows = W.recorded()
+        second = rows[4:8]                      # the block-on-block pair's four points, second step
+        assert len(second) == 4
+        assert int(second[:, 22].sum()) == n_matched
+        assert np.all(second[second[:, 22] == 0, 19:22] == 0)
+        if n_matched == 4:
+            assert abs(second[:, 19].sum() - 0.015 / 0.015) < 1e-6   # previous total normal impulse m g h
