@@ -107,3 +107,24 @@ def test_binding_struct_layouts_match_the_header():
         assert int(got[n]) == C.sizeof(m), n
         for f, _ in m._fields_:
             assert int(got[f"{n}.{cname(f)}"]) == getattr(m, f).offset, (n, f)
+
+
+def test_too_small_workspace_is_refused_before_any_device_work():
+    """A workspace smaller than jb_workspace_bytes is refused with
+    JB_ENOMEM from the host-side size check (no device memory is touched,
+    so a dummy address is safe)."""
+    import paper_2606_28394_gb300 as jb
+    sc = synth.build_scene([synth.Tower(levels=2)], 0)
+    prm = jb.default_params()
+    arrs = [np.ascontiguousarray(a, t) for a, t in ((sc.body_off, np.int32), (sc.half, np.float32),
+                                                   (sc.mass, np.float32), (sc.mu, np.float32),
+                                                   (sc.x, np.float32), (sc.q, np.float32), (sc.v, np.float32),
+                                                   (sc.w, np.float32), (sc.ground_mu, np.float32))]
+    fp = lambda a: a.ctypes.data_as(C.POINTER(C.c_float))
+    scene = jb.jb_scene(1, arrs[0].ctypes.data_as(C.POINTER(C.c_int32)), *[fp(a) for a in arrs[1:]])
+    need = jb.jb_workspace_bytes(1, arrs[0].ctypes.data_as(C.POINTER(C.c_int32)), C.byref(prm), 0)
+    assert need > 256
+    h = C.c_void_p()
+    rc = jb.jb_batch_create(C.byref(scene), C.byref(prm), 0, C.c_void_p(0x1000), need - 256, None, C.byref(h))
+    assert rc == jb.JB_ENOMEM and not h.value
+    assert b"too small" in jb.jb_last_error()

@@ -178,3 +178,23 @@ def test_reference_episode_search(cuda_device):
         want = (min(cand, key=lambda e: (abs(removed[e] - n_hat), e)) if cand
                 else min(range(len(towers)), key=lambda e: (-st["moves_done"][e], e)))
         assert b.reference_episode(n_hat) == (want, removed[want])
+
+
+def test_nonfinite_episode_is_isolated(cuda_device):
+    """Fault injection on the host: a NaN velocity written into one body of
+    the middle episode.  That episode is flagged non-finite and stops; its
+    neighbours run exactly as in a batch without the NaN."""
+    towers = [synth.Tower(levels=4), synth.Tower(levels=4), synth.Tower(levels=4)]
+    sc = synth.build_scene(towers, 12)
+    prm = synth.params(residual_tol=1e-5, pgs_iter_cap=20000)
+    clean, bad = jb().Batch(sc, prm), jb().Batch(sc, prm)
+    v = sc.v.astype(np.float32).copy()
+    v[0, 12 + 5] = np.nan
+    bad.write_state(v=v)
+    clean.step(3)
+    bad.step(3)
+    st = bad.stats()
+    assert st["status"][1] & jb().JB_EP_NONFINITE
+    assert st["status"][0] == 0 and st["status"][2] == 0
+    for u, w in zip(clean.state(), bad.state()):
+        assert np.array_equal(u[:, :12], w[:, :12]) and np.array_equal(u[:, 24:], w[:, 24:])
