@@ -1,21 +1,25 @@
 // Device kernels of the batched rigid-body step (sm_103a).
 //
 // One warp owns one episode (a tower) for the whole launch: the episode's
-// bodies live in shared memory, its contact pairs and points in an L1/L2
-// resident global workspace.  A persistent grid claims episodes from a work
-// counter.  Per substep the warp runs (paper sections in brackets):
+// bodies and, when they fit, its colour-sorted contact pairs and points live
+// in shared memory; the natural-order contact records (and the solver arrays
+// of steps with more pairs than fit) live in the global workspace.  A
+// persistent grid claims episodes from a work counter.  Per substep the warp
+// runs (paper sections in brackets):
 //   forces and frames [Sec. 4.2, Eq. rotmat]
 //   broadphase, all pairs, ballot compaction in natural order [Sec. 6.1, Eq. aabb]
 //   SAT over 15 axes + face-clipped manifold, one pair per lane [Sec. 6.2, 6.2.1]
 //   warm-start matching against the previous step's contacts
-//   greedy edge colouring of the contact graph (colours persist across steps)
-//   contact setup [Sec. 7.1, Eq. keff]
+//   greedy edge colouring of the contact graph, redone every step
+//   contact setup [Sec. 7.1, Eq. keff]; optionally the learned warm start
 //   coloured projected Gauss-Seidel: pairs of one colour share no dynamic body
-//   and run in parallel, colours in sequence [Sec. 7.1-7.3, Eq. lambda_n,
-//   Eq. coulomb_pgs]; residual mode sweeps until the residual <= tol
+//   and run in parallel, one per lane, colours in sequence [Sec. 7.1-7.3,
+//   Eq. lambda_n, Eq. coulomb_pgs]; residual mode sweeps until the residual
+//   <= tol, checked at an adaptive cadence
 //   integration [Sec. 4.2, Eq. quat_int] and position correction [Eq. baumgarte]
 //   collapse / rest bookkeeping and the push schedule [Sec. 5, Sec. 8]
-// Everything is FP32.  Waits are warp barriers only; every loop is bounded.
+// Everything is FP32 (the network's operands BF16).  Waits are warp barriers
+// only; every loop is bounded.
 #include <cfloat>
 #include <cstdint>
 
