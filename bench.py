@@ -337,8 +337,9 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(c["seconds"] for c in vals),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "450 episodes x 18-level towers, mu {0.25,0.40,0.60}, removal rounds",
-                       "residual_tol": args.tol, "sample": vals[0]["sample"]},
+            "config": {"workload": WORKLOAD_NAME[args.workload] if not args.episodes else
+                       f"{args.episodes} episodes (evenly spaced) of: {WORKLOAD_NAME[args.workload]}",
+                       "residual_tol": args.tol, "pgs_iter_cap": args.cap, "sample": vals[0]["sample"]},
             "cpu_baseline": {k: vals[0][k] for k in ("kind", "cores", "sample")} | {"value": v, "unit": "body-steps/s"},
             "e2e": {"value": v, "unit": "body-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
