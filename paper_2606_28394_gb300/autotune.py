@@ -56,16 +56,36 @@ def _key(scene, params, gpu):
     return f"{gpu}:{h.hexdigest()[:16]}"
 
 
-def tune(scene, prot, params, trial_steps=120, sample=64, device="cuda", use_cache=True, log=None):
+def _gpu_trial(s, p, prm, trial_steps, device):
+    """Milliseconds (CUDA events) of `trial_steps` steps of the sample."""
+    import torch
+    b = Batch(s, prm, max_moves=int(p.off[-1]), device=device)
+    b.set_protocol(p)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(b.stream)
+    b.run_protocol(trial_steps)
+    e1.record(b.stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def tune(scene, prot, params, trial_steps=120, sample=64, device="cuda", use_cache=True, log=None,
+         trial=None, gpu_name=None, cache_path=None):
     """Returns a copy of params with the fastest (smem_pair_factor,
     residual_every, residual_every_max) on a trial of the workload, and the
-    timing table."""
-    import torch
-    gpu = torch.cuda.get_device_name(torch.device(device))
-    key = _key(scene, params, gpu)
+    timing table.  `trial(scene, prot, params) -> ms`, `gpu_name` and
+    `cache_path` default to timing the library on the current GPU and the
+    package's cache file."""
+    if gpu_name is None:
+        import torch
+        gpu_name = torch.cuda.get_device_name(torch.device(device))
+    if trial is None:
+        trial = lambda s, p, prm: _gpu_trial(s, p, prm, trial_steps, device)
+    cache_path = cache_path or CACHE
+    key = _key(scene, params, gpu_name)
     cache = {}
-    if use_cache and os.path.exists(CACHE):
-        with open(CACHE) as f:
+    if use_cache and os.path.exists(cache_path):
+        with open(cache_path) as f:
             cache = json.load(f)
     if key in cache:
         return dict(params, **cache[key]["best"]), cache[key]["table"]
@@ -75,14 +95,7 @@ def tune(scene, prot, params, trial_steps=120, sample=64, device="cuda", use_cac
     for fac in FACTORS:
         for ev, evm in CADENCE:
             prm = dict(params, smem_pair_factor=fac, residual_every=ev, residual_every_max=evm)
-            b = Batch(s, prm, max_moves=int(p.off[-1]), device=device)
-            b.set_protocol(p)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(b.stream)
-            b.run_protocol(trial_steps)
-            e1.record(b.stream)
-            torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1)
+            ms = trial(s, p, prm)
             table.append({"smem_pair_factor": fac, "residual_every": ev, "residual_every_max": evm, "ms": ms})
             if log:
                 log(f"factor {fac} cadence {ev}..{evm}: {ms:.1f} ms")
@@ -90,6 +103,6 @@ def tune(scene, prot, params, trial_steps=120, sample=64, device="cuda", use_cac
     choice = {k: best[k] for k in TUNED}
     if use_cache:
         cache[key] = {"best": choice, "table": table}
-        with open(CACHE, "w") as f:
+        with open(cache_path, "w") as f:
             json.dump(cache, f, indent=1)
     return dict(params, **choice), table
