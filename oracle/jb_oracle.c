@@ -71,6 +71,8 @@ typedef struct {
   double ground_mu;
   or_pair *pairs, *prev;
   int np, cap, nprev, capprev;
+  int* order;            /* sweep order of the pairs (colour_order); ocap entries */
+  int ocap;
   /* schedule */
   int n_moves, mi, phase, remaining, pb, rest_left;
   const int *mv_block, *mv_axis, *mv_remove, *mv_push, *mv_settle;
@@ -634,9 +636,50 @@ static void disc_project(double a1, double a2, double lim, double* p1, double* p
   *p2 = a2 * s;
 }
 
+static int cmp_int2(const void* x, const void* y) {
+  const int *a = (const int*)x, *b = (const int*)y;
+  if (a[0] != b[0]) return a[0] < b[0] ? -1 : 1;
+  return (a[1] > b[1]) - (a[1] < b[1]);
+}
+
+/* The sweep order of this solve: natural, or the GPU library's colour order
+   (see or_params.colour_order).  Only the order of the pair updates
+   changes; the rows of a pair and the fixed point do not. */
+static void sweep_order(or_episode* E, int colour) {
+  const int n = E->np;
+  if (E->ocap < n) { E->ocap = n + 64; E->order = (int*)realloc(E->order, sizeof(int) * E->ocap); }
+  for (int i = 0; i < n; ++i) E->order[i] = i;
+  if (!colour || n <= 0) return;
+  int (*kv)[2] = (int(*)[2])malloc(sizeof(int) * 2 * (size_t)n);
+  for (int i = 0; i < n; ++i) {
+    kv[i][0] = (int)floor((E->pairs[i].p[0][2] + 5e-4) * 1000.0) + 1;   /* 1 mm height bin */
+    kv[i][1] = -i;                                                    /* then index descending */
+  }
+  qsort(kv, n, sizeof(int) * 2, cmp_int2);
+  unsigned long long* used = (unsigned long long*)calloc(E->nb + 1, sizeof(unsigned long long));
+  int* col = (int*)malloc(sizeof(int) * (size_t)n);
+  for (int t = 0; t < n; ++t) {
+    const int p = -kv[t][1];
+    const int a = E->pairs[p].a, b = E->pairs[p].b;
+    const int sa = a < 0 || E->b[a].is_static, sb = E->b[b].is_static;
+    const unsigned long long m = (sa ? 0ull : used[a]) | (sb ? 0ull : used[b]);
+    int c = 0;
+    while (c < 63 && ((m >> c) & 1ull)) ++c;   /* colour 63 collects the overflow */
+    if (c < 63) {
+      if (!sa) used[a] |= 1ull << c;
+      if (!sb) used[b] |= 1ull << c;
+    }
+    col[p] = c;
+  }
+  for (int i = 0; i < n; ++i) { kv[i][0] = col[i]; kv[i][1] = i; }
+  qsort(kv, n, sizeof(int) * 2, cmp_int2);
+  for (int i = 0; i < n; ++i) E->order[i] = kv[i][1];
+  free(kv); free(used); free(col);
+}
+
 static void pgs_sweep(or_episode* E, double e, int cone) {
-  for (int c = 0; c < E->np; ++c) {
-    or_pair* pr = &E->pairs[c];
+  for (int cc = 0; cc < E->np; ++cc) {
+    or_pair* pr = &E->pairs[E->order[cc]];
     or_body *A = body_ref(E, pr->a), *B = body_ref(E, pr->b);
     const double* dirs[3] = {pr->n, pr->t1, pr->t2};
     for (int i = 0; i < pr->np; ++i) {
@@ -714,6 +757,7 @@ static double pgs_residual(or_episode* E, int cone) {
 }
 
 static void solve(or_episode* E, const or_params* P) {
+  sweep_order(E, P->colour_order);
   int sweeps = 0;
   double res = 0;
   if (E->np > 0) {
@@ -1041,7 +1085,7 @@ or_world* or_create(int n_episodes, const int* body_off, const double* half, con
 
 void or_destroy(or_world* W) {
   if (!W) return;
-  for (int e = 0; e < W->E; ++e) { free(W->ep[e].b); free(W->ep[e].pairs); free(W->ep[e].prev); }
+  for (int e = 0; e < W->E; ++e) { free(W->ep[e].b); free(W->ep[e].pairs); free(W->ep[e].prev); free(W->ep[e].order); }
   free(W->ep); free(W->body_off);
   free(W->m_block); free(W->m_axis); free(W->m_remove); free(W->m_push); free(W->m_settle);
   free(W->m_sign); free(W->m_factor); free(W->m_k);

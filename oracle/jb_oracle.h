@@ -47,6 +47,12 @@ typedef struct {
                             and a touching point approaching faster than restitution_vmin
                             targets v_n = -e v_n(pre-solve) */
   double restitution_vmin; /* m/s; <= 0 selects 2 |g| h */
+  int colour_order;      /* 0: Gauss-Seidel in natural pair order (the listing); 1: in the GPU
+                            library's colour order, for comparing fixed-iteration results:
+                            greedy lowest-free colouring of the pairs taken by (contact height of
+                            their first point in 1 mm bins ascending, natural index descending),
+                            colours ascending, natural index ascending within a colour.  Static
+                            bodies (the ground) do not constrain the colouring.  Same fixed point. */
 } or_params;
 
 /* episode statistics, one row of OR_NSTAT doubles per episode */

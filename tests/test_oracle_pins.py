@@ -741,3 +741,21 @@ def test_oracle_is_independent_of_thread_count():
         out.append(W.state())
     for a, b in zip(*out):
         assert np.array_equal(a, b)
+
+
+def test_colour_order_keeps_the_fixed_point():
+    """The optional colour sweep order (the GPU library's) changes the
+    iterates, not the fixed point: converged tightly, a perturbed tower's
+    velocities agree with the natural order's; after 20 fixed sweeps they
+    differ (the option takes effect)."""
+    sc = synth.perturbed(synth.build_scene([synth.Tower(levels=4, mu=0.5)], 1), 5, dx=2e-4, dang=0.01)
+    s64 = synth.Scene(sc.body_off, *[getattr(sc, k).astype(np.float64) for k in
+                                     ("half", "mass", "mu", "x", "q", "v", "w", "ground_mu")])
+    out = {}
+    for name, prm in (("conv", dict(residual_tol=1e-11, pgs_iter_cap=2000000)), ("fixed", dict(pgs_iters=20))):
+        for order in (0, 1):
+            W = oracle.World(s64, synth.params(colour_order=order, **prm))
+            W.step(1)
+            out[name, order] = W.state()
+    assert np.abs(out["conv", 0][2] - out["conv", 1][2]).max() < 1e-7
+    assert np.abs(out["fixed", 0][2] - out["fixed", 1][2]).max() > 1e-5
