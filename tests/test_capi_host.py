@@ -128,3 +128,41 @@ def test_too_small_workspace_is_refused_before_any_device_work():
     rc = jb.jb_batch_create(C.byref(scene), C.byref(prm), 0, C.c_void_p(0x1000), need - 256, None, C.byref(h))
     assert rc == jb.JB_ENOMEM and not h.value
     assert b"too small" in jb.jb_last_error()
+
+
+def _scene_struct(jb, sc, keep):
+    arrs = [np.ascontiguousarray(a, t) for a, t in ((sc.body_off, np.int32), (sc.half, np.float32),
+                                                   (sc.mass, np.float32), (sc.mu, np.float32),
+                                                   (sc.x, np.float32), (sc.q, np.float32), (sc.v, np.float32),
+                                                   (sc.w, np.float32), (sc.ground_mu, np.float32))]
+    keep.extend(arrs)
+    fp = lambda a: a.ctypes.data_as(C.POINTER(C.c_float))
+    return jb.jb_scene(sc.n_episodes, arrs[0].ctypes.data_as(C.POINTER(C.c_int32)), *[fp(a) for a in arrs[1:]])
+
+
+def test_corrupt_inputs_are_refused_before_any_device_work():
+    """Host-side validation of jb_batch_create (error codes and messages; no
+    device memory is touched, so a dummy workspace address is safe):
+    non-positive half extents, a decreasing body_off, and out-of-range solver
+    parameters are JB_EINVAL."""
+    import paper_2606_28394_gb300 as jb
+    good = synth.build_scene([synth.Tower(levels=2), synth.Tower(levels=1)], 0)
+    cases = []
+    sc = synth.build_scene([synth.Tower(levels=2), synth.Tower(levels=1)], 0)
+    sc.half[1, 3] = 0.0
+    cases.append(("half extents", sc, {}))
+    sc = synth.build_scene([synth.Tower(levels=2), synth.Tower(levels=1)], 0)
+    sc.body_off = np.array([0, 6, 4, 9], np.int32)
+    cases.append(("body_off", sc, {}))
+    for bad in (dict(sor=2.5), dict(friction_cone=3), dict(residual_every=0), dict(warm_start=7),
+                dict(dt=0.0), dict(restitution_newton=2), dict(stall_window=-1)):
+        cases.append((None, good, bad))
+    for expect, sc, bad in cases:
+        keep = []
+        scene = _scene_struct(jb, sc, keep)
+        p = jb.default_params(**bad)
+        h = C.c_void_p()
+        rc = jb.jb_batch_create(C.byref(scene), C.byref(p), 0, C.c_void_p(0x1000), 1 << 30, None, C.byref(h))
+        assert rc == jb.JB_EINVAL and not h.value, (expect, bad)
+        if expect:
+            assert expect.encode() in jb.jb_last_error(), jb.jb_last_error()
