@@ -235,12 +235,14 @@ class Batch:
 
     # -- schedule and stepping
     def set_params(self, params):
+        """Replace the solver parameters (jb_set_params); smem_pair_factor is fixed at creation."""
         if isinstance(params, dict):
             params = params_from_dict(params)
         self.params = params
         check(jb_set_params(self.h, C.byref(params)), "jb_set_params")
 
     def set_protocol(self, prot):
+        """Upload the push/removal schedule (CSR over episodes) and start every episode's first move."""
         arrs = [_i32(prot.off), _i32(prot.block), _i32(prot.axis), _f32(prot.sign),
                 _f32(prot.factor), _f32(prot.k), _i32(prot.remove), _i32(prot.push_steps),
                 _i32(prot.settle_steps)]
@@ -249,18 +251,24 @@ class Batch:
         check(jb_set_protocol(self.h, C.byref(pr)), "jb_set_protocol")
 
     def run_protocol(self, max_steps=1 << 30):
+        """Run every unfinished episode through its schedule, at most max_steps steps, in one
+        persistent launch per size class (asynchronous on the batch stream)."""
         check(jb_run_protocol(self.h, int(max_steps)), "jb_run_protocol")
 
     def step(self, n=1):
+        """Advance every episode n steps with no schedule (host-driven; asynchronous)."""
         check(jb_step(self.h, int(n)), "jb_step")
 
     def apply_push(self, episode, block, axis, force, n_steps):
+        """Constant force (N, signed) along a block's X (width) or Y (length) axis at its
+        centre of mass for n_steps steps; arrays or scalars, episode-local block ids."""
         ep, bl, ax, st = (_i32(np.atleast_1d(a)) for a in (episode, block, axis, n_steps))
         f = _f32(np.atleast_1d(force))
         check(jb_apply_push(self.h, len(ep), _pi(ep), _pi(bl), _pi(ax), _pf(f), _pi(st)),
               "jb_apply_push")
 
     def remove_block(self, episode, block):
+        """Take blocks out of the simulation (inactive from the next step)."""
         ep, bl = _i32(np.atleast_1d(episode)), _i32(np.atleast_1d(block))
         check(jb_remove_block(self.h, len(ep), _pi(ep), _pi(bl)), "jb_remove_block")
 
@@ -280,12 +288,14 @@ class Batch:
         return [(int(e[i]), int(nb[i]), int(g[i])) for i in range(n.value)]
 
     def sync(self):
+        """Wait for queued work; returns the number of episodes with a non-zero status."""
         n = C.c_int32(0)
         check(jb_sync(self.h, C.byref(n)), "jb_sync")
         return n.value
 
     # -- readback
     def state(self):
+        """(x [3,B], q [4,B], v [3,B], w [3,B]) as float32 host arrays."""
         x = np.zeros((3, self.B), np.float32); q = np.zeros((4, self.B), np.float32)
         v = np.zeros((3, self.B), np.float32); w = np.zeros((3, self.B), np.float32)
         check(jb_read_state(self.h, x.ctypes.data, q.ctypes.data, v.ctypes.data, w.ctypes.data, 0),
@@ -293,17 +303,21 @@ class Batch:
         return x, q, v, w
 
     def write_state(self, x=None, q=None, v=None, w=None, clear_cache=False, reset_reference=False):
+        """Overwrite any of x, q, v, w (host arrays); optionally forget the warm-start cache
+        or take the new poses as the collapse reference."""
         arrs = [None if a is None else _f32(a) for a in (x, q, v, w)]
         ptrs = [None if a is None else a.ctypes.data for a in arrs]
         check(jb_write_state(self.h, *ptrs, 0, int(clear_cache), int(reset_reference)),
               "jb_write_state")
 
     def active(self):
+        """Per-body flags: True while the body is in the simulation."""
         a = np.zeros(self.B, np.int32)
         check(jb_read_active(self.h, _pi(a)), "jb_read_active")
         return a.astype(bool)
 
     def contacts(self, episode):
+        """The last substep's contact points of one episode (list of jb_contact)."""
         n = C.c_int32(0)
         check(jb_read_contacts(self.h, int(episode), None, 0, C.byref(n)), "jb_read_contacts")
         buf = (jb_contact * max(n.value, 1))()
@@ -311,6 +325,7 @@ class Batch:
         return [buf[i] for i in range(n.value)]
 
     def stats(self):
+        """Per-episode statistics as a dict of arrays (jb_episode_stats fields)."""
         buf = (jb_episode_stats * self.E)()
         check(jb_read_episode_stats(self.h, buf), "jb_read_episode_stats")
         out = {}
@@ -319,12 +334,14 @@ class Batch:
         return out
 
     def save_state(self):
+        """Snapshot of the batch's device state as a host byte array (jb_save_state)."""
         n = jb_state_bytes(self.h)
         buf = np.empty(n, np.uint8)
         check(jb_save_state(self.h, buf.ctypes.data, n), "jb_save_state")
         return buf
 
     def load_state(self, buf):
+        """Restore a snapshot taken by save_state on a batch of the same shape."""
         buf = np.ascontiguousarray(buf, np.uint8)
         check(jb_load_state(self.h, buf.ctypes.data, buf.nbytes), "jb_load_state")
 
