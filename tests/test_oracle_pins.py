@@ -759,3 +759,83 @@ def test_colour_order_keeps_the_fixed_point():
             out[name, order] = W.state()
     assert np.abs(out["conv", 0][2] - out["conv", 1][2]).max() < 1e-7
     assert np.abs(out["fixed", 0][2] - out["fixed", 1][2]).max() > 1e-5
+
+
+# --------------------------------------------- Sec. 6.2.1 reduction to 4 points
+def _hull_area_xy(P):
+    """Largest polygon area over the orderings of a few xy points (brute
+    force); for points in convex position, as any subset of an octagon's
+    corners is, that is the area of their convex hull."""
+    import itertools
+    best = 0.0
+    for perm in itertools.permutations(range(1, len(P))):
+        idx = (0,) + perm
+        s = sum(P[idx[i]][0] * P[idx[(i + 1) % len(P)]][1] - P[idx[(i + 1) % len(P)]][0] * P[idx[i]][1]
+                for i in range(len(P)))
+        best = max(best, abs(s) / 2)
+    return best
+
+
+def test_reduce_octagon_keeps_the_largest_inscribed_quad():
+    # two square-topped blocks, the upper turned 45 deg about z: the overlap of
+    # the faces is an octagon (8 clipped points, all at the same depth), so the
+    # reduction to 4 points runs.  Its picks (deepest, farthest, largest
+    # triangle, largest added area) give the largest-area 4-subset, which brute
+    # force over all 70 subsets of the octagon's closed-form corners finds.
+    import itertools
+    a, hz, pen, eps = 0.0125, 0.0075, 2e-4, 1e-6
+    half = (a, a, hz)
+    m = oracle.pair_manifold(np.zeros(3), [1, 0, 0, 0], half, [0, 0, 2 * hz - pen],
+                             qaxis((0, 0, 1), math.pi / 4), half)
+    assert m["np"] == 4 and m["axis"] == 2 and np.allclose(m["n"], [0, 0, 1])
+    assert np.allclose(m["depth"], pen, atol=1e-13)
+    # the incident face's edges |x| + |y| = a sqrt2 cut A's side planes, taken
+    # eps outward, at |x| = a + eps or |y| = a + eps
+    s = a * math.sqrt(2) - (a + eps)
+    octagon = [(sx * (a + eps), sy * s) for sx in (-1, 1) for sy in (-1, 1)] + \
+              [(sx * s, sy * (a + eps)) for sx in (-1, 1) for sy in (-1, 1)]
+    for p in m["p"]:
+        assert min(math.hypot(p[0] - c[0], p[1] - c[1]) for c in octagon) < 1e-12
+        assert abs(p[2] - (hz - pen / 2)) < 1e-13
+    best = max(_hull_area_xy(sub) for sub in itertools.combinations(octagon, 4))
+    kept = _hull_area_xy([tuple(p[:2]) for p in m["p"]])
+    assert kept == pytest.approx(best, rel=1e-12)
+    # and it is far from what the first four clipped points would give
+    assert best > 1.9 * a * a
+
+
+def test_reduce_tilted_octagon_keeps_the_deepest_point_first():
+    # the same octagon with the upper block tilted by 3 mrad about a generic
+    # horizontal axis: depth is linear over the overlap, so its maximum sits at
+    # a corner, and a linear program over the overlap (the incident face's
+    # square mapped into A's top rectangle) gives it independently of clipping.
+    from scipy.optimize import linprog
+    a, hz, pen, eps = 0.0125, 0.0075, 2e-4, 1e-6
+    half = (a, a, hz)
+    qB = qmul(qaxis((1, 0.3, 0), 3e-3), qaxis((0, 0, 1), math.pi / 4))
+    xB = np.array([0.0, 0.0, 2 * hz - pen])
+    m = oracle.pair_manifold(np.zeros(3), [1, 0, 0, 0], half, xB, qB, half)
+    assert m["np"] == 4 and m["axis"] == 2 and np.allclose(m["n"], [0, 0, 1])
+    # B's bottom face: c + u ex + v ey, u, v in [-1, 1]
+    R = rodrigues((1, 0.3, 0), 3e-3) @ rodrigues((0, 0, 1), math.pi / 4)
+    c = xB - hz * R[:, 2]
+    ex, ey = a * R[:, 0], a * R[:, 1]
+    # maximise depth hz - z(u, v) = minimise z(u, v) subject to |x|, |y| <= a + eps
+    A_ub, b_ub = [], []
+    for k in (0, 1):
+        A_ub += [[ex[k], ey[k]], [-ex[k], -ey[k]]]
+        b_ub += [a + eps - c[k], a + eps + c[k]]
+    lp = linprog([ex[2], ey[2]], A_ub=A_ub, b_ub=b_ub, bounds=[(-1, 1), (-1, 1)], method="highs")
+    assert lp.status == 0
+    dmax = hz - (c[2] + lp.fun)
+    d = np.asarray(m["depth"][:4])
+    assert d[0] == pytest.approx(dmax, abs=1e-9)
+    assert d.max() == pytest.approx(dmax, abs=1e-9)
+    assert np.ptp(d) > 1e-5              # the tilt spreads the depths
+    # every kept point is the midpoint of an incident-face point in the overlap
+    nB = R[:, 2]
+    for p, dep in zip(m["p"][:4], d):
+        inc = p - np.array([0, 0, dep / 2])
+        assert abs(np.dot(inc - c, nB)) < 1e-12
+        assert abs(inc[0]) <= a + eps + 1e-12 and abs(inc[1]) <= a + eps + 1e-12
+        assert dep == pytest.approx(hz - inc[2], abs=1e-13)
