@@ -839,3 +839,22 @@ def test_reduce_tilted_octagon_keeps_the_deepest_point_first():
         assert abs(np.dot(inc - c, nB)) < 1e-12
         assert abs(inc[0]) <= a + eps + 1e-12 and abs(inc[1]) <= a + eps + 1e-12
         assert dep == pytest.approx(hz - inc[2], abs=1e-13)
+
+
+def test_side_contact_tangent_basis_and_points():
+    # B beside A along x, 1 mm higher in y: the contact normal is world X, so
+    # the tangent basis takes its other branch (t1 from world Y, since world X
+    # is parallel to n); the manifold is B's end face clipped by A's side
+    # planes y = +-hy, z = +-hz, each taken 1 um outward.
+    pen, dy = 1.5e-4, 1e-3
+    hx, hy, hz = HALF
+    m = oracle.pair_manifold(np.zeros(3), [1, 0, 0, 0], HALF, [2 * hx - pen, dy, 0.0], [1, 0, 0, 0], HALF)
+    assert m["np"] == 4 and m["axis"] == 0
+    assert np.allclose(m["n"], [1, 0, 0])
+    assert np.allclose(m["t1"], [0, 1, 0], atol=1e-15)
+    t2 = np.cross(m["n"], m["t1"])
+    assert np.allclose(t2, [0, 0, 1], atol=1e-15)
+    assert np.allclose(m["depth"], pen, atol=1e-13)
+    exp = np.array([(hx - pen / 2, y, z) for y in (dy - hy, hy + 1e-6) for z in (-hz, hz)])
+    dist = np.linalg.norm(m["p"][:4, None, :] - exp[None, :, :], axis=2)
+    assert sorted(dist.argmin(axis=1)) == [0, 1, 2, 3] and dist.min(axis=1).max() < 1e-12
