@@ -858,3 +858,32 @@ def test_side_contact_tangent_basis_and_points():
     exp = np.array([(hx - pen / 2, y, z) for y in (dy - hy, hy + 1e-6) for z in (-hz, hz)])
     dist = np.linalg.norm(m["p"][:4, None, :] - exp[None, :, :], axis=2)
     assert sorted(dist.argmin(axis=1)) == [0, 1, 2, 3] and dist.min(axis=1).max() < 1e-12
+
+
+# ------------------------------------------------------ Sec. 6.1 broadphase
+@pytest.mark.parametrize("n,seed,spread,height", [(32, 0, 0.07, 0.04), (24, 7, 0.05, 0.03), (40, 11, 0.12, 0.06)])
+def test_broadphase_drops_no_pair_the_narrowphase_keeps(n, seed, spread, height):
+    # the AABB test (Eq. aabb) only prunes: on a dense pile of randomly turned
+    # blocks the oracle's contact set after one step's detection equals the
+    # narrowphase run on every pair and on every body against the ground.
+    # (A world-frame extent built from the transposed rotation drops real
+    # pairs of the first pile.)  The piles differ in size, not only in seed.
+    sc = synth.pile_scene(n_boxes=n, seed=seed, spread=spread, height=height)
+    prm = synth.params()
+    W = oracle.World(sc, prm)
+    x, q, _, _ = W.state()
+    W.step(1)
+    got = {(int(c[0]), int(c[1])): int(c[5]) for c in W.contacts(0)}
+    m, h = prm["contact_margin"], sc.half
+    exp = {}
+    for j in range(n):
+        k = oracle.ground_manifold(x[:, j], q[:, j], h[:, j], m)["np"]
+        if k:
+            exp[(-1, j)] = k
+    for i in range(n):
+        for j in range(i + 1, n):
+            k = oracle.pair_manifold(x[:, i], q[:, i], h[:, i], x[:, j], q[:, j], h[:, j], m)["np"]
+            if k:
+                exp[(i, j)] = k
+    assert len(exp) > 2 * n
+    assert got == exp
