@@ -887,3 +887,85 @@ def test_broadphase_drops_no_pair_the_narrowphase_keeps(n, seed, spread, height)
                 exp[(i, j)] = k
     assert len(exp) > 2 * n
     assert got == exp
+
+
+# ------------------------------------------- Sec. 7 the LCP the solver converges to
+@pytest.mark.parametrize("cone", [0, 1])
+@pytest.mark.parametrize("n,seed,spread,height", [(12, 0, 0.10, 0.04), (20, 7, 0.08, 0.05), (16, 300, 0.06, 0.03)])
+def test_converged_step_satisfies_the_contact_lcp_and_newton_euler(cone, n, seed, spread, height):
+    # After a step solved to residual 1e-12 m/s, every contact point must meet
+    # the conditions that define the solution, computed here from the step's
+    # own output and not from the solver's rows:
+    #   lambda_n >= 0, u_n + b >= 0, lambda_n (u_n + b) = 0, with u the relative
+    #   velocity of B against A at the point after the step and b = max(0, -depth)/h;
+    #   friction within mu lambda_n, mu = the smaller of the two bodies' mu_s;
+    #   sticking (inside the limit): u_t = 0; sliding (on it): the impulse
+    #   opposes u_t (box: per tangent row; cone: along the disc's radius).
+    # And the velocity change of every body equals its contact impulses through
+    # the box's closed-form inertia (Newton-Euler; gravity adds h g).  The
+    # blocks carry different mu_s to tell the pair rule from either body's.
+    h = 1.0 / 240
+    tol_v, tol_p = 5e-12, 1e-13
+    sc = synth.pile_scene(n_boxes=n, seed=seed, spread=spread, height=height)
+    sc.mu = np.linspace(0.2, 0.7, n)[np.argsort(np.arange(n) * 7 % n)].astype(sc.mu.dtype)
+    prm = synth.params(residual_tol=1e-12, pgs_iter_cap=400000, friction_cone=cone)
+    W = oracle.World(sc, prm)
+    W.step(3)                                   # warm contacts: friction and the cache in play
+    x0, q0, v0, w0 = W.state()
+    W.step(1)
+    _, _, v1, w1 = W.state()
+    assert W.stats()["last_residual"][0] <= 1e-12
+    g = np.asarray(prm["gravity"], float)
+    lin, ang = np.zeros((3, n)), np.zeros((3, n))
+    counts = dict(stick=0, slide=0, spec=0)
+    for c in oracle.contact_dicts(W.contacts(0)):
+        a, b = c["a"], c["b"]
+        mu = min(float(sc.ground_mu[0]) if a < 0 else float(sc.mu[a]), float(sc.mu[b]))
+        nrm, t1 = c["n"], c["t1"]
+        t2 = np.cross(nrm, t1)
+        for i in range(c["np"]):
+            p, (ln, l1, l2) = c["p"][i], c["lam"][i]
+            P = ln * nrm + l1 * t1 + l2 * t2
+            rB = p - x0[:, b]
+            u = v1[:, b] + np.cross(w1[:, b], rB)
+            lin[:, b] += P; ang[:, b] += np.cross(rB, P)
+            if a >= 0:
+                rA = p - x0[:, a]
+                u = u - v1[:, a] - np.cross(w1[:, a], rA)
+                lin[:, a] -= P; ang[:, a] -= np.cross(rA, P)
+            un, ut = u @ nrm, np.array([u @ t1, u @ t2])
+            bias = max(0.0, -c["depth"][i]) / h
+            counts["spec"] += c["depth"][i] < 0
+            assert ln >= 0.0 and un + bias >= -tol_v
+            assert ln == 0.0 or abs(un + bias) <= tol_v
+            lim, lt = mu * ln, np.array([l1, l2])
+            if lim <= 1e-15:
+                assert not lt.any()
+                continue
+            if cone:
+                r = np.hypot(*lt)
+                assert r <= lim * (1 + 1e-12)
+                if r < lim * (1 - 1e-6):
+                    counts["stick"] += 1
+                    assert np.hypot(*ut) <= tol_v
+                else:
+                    counts["slide"] += 1
+                    d = lt / r
+                    assert ut @ d <= tol_v and abs(ut[0] * d[1] - ut[1] * d[0]) <= tol_v
+            else:
+                assert np.all(np.abs(lt) <= lim * (1 + 1e-12))
+                for lk, uk in zip(lt, ut):
+                    if abs(lk) < lim * (1 - 1e-6):
+                        assert abs(uk) <= tol_v
+                    else:
+                        assert np.sign(lk) * uk <= tol_v
+                inside = np.abs(lt) < lim * (1 - 1e-6)
+                counts["stick" if inside.all() else "slide"] += 1
+    assert counts["stick"] >= 4 and counts["slide"] >= 10 and counts["spec"] >= 2
+    m = np.asarray(sc.mass, float)
+    assert np.abs(m * (v1 - v0 - h * g[:, None]) - lin).max() <= tol_p
+    for j in range(n):
+        hx, hy, hz = np.asarray(sc.half[:, j], float)
+        I = m[j] / 3.0 * np.array([hy * hy + hz * hz, hx * hx + hz * hz, hx * hx + hy * hy])
+        R = oracle.rotmat(q0[:, j])
+        assert np.abs(w1[:, j] - w0[:, j] - R @ ((R.T @ ang[:, j]) / I)).max() <= 1e-10
