@@ -969,3 +969,26 @@ def test_converged_step_satisfies_the_contact_lcp_and_newton_euler(cone, n, seed
         I = m[j] / 3.0 * np.array([hy * hy + hz * hz, hx * hx + hz * hz, hx * hx + hy * hy])
         R = oracle.rotmat(q0[:, j])
         assert np.abs(w1[:, j] - w0[:, j] - R @ ((R.T @ ang[:, j]) / I)).max() <= 1e-10
+
+
+# ------------------------------------------------ Sec. 5 the push/removal schedule
+def test_schedule_counts_steps_moves_and_body_steps_by_definition():
+    # three sub-threshold moves on a 6-level tower: push block 4 (level 1,
+    # middle) for 30 steps and remove it, settle 50; push block 10 for 20
+    # steps, no removal, no settle; push block 7 for 15, remove it, settle 25.
+    # Nothing collapses, so the schedule alone fixes every count: 140 steps,
+    # 3 moves, blocks 4 and 7 gone, and sum(steps x dynamic bodies) body-steps
+    # with a removal taking effect after its push.
+    sc = synth.build_scene([synth.Tower(levels=6, mu=0.4)], 0)
+    moves = [(4, synth.AXIS_Y, 1.0, 0.3, 3.0, 1, 30, 50),
+             (10, synth.AXIS_X, -1.0, 0.3, 4.0, 0, 20, 0),
+             (7, synth.AXIS_Y, 1.0, 0.3, 3.0, 1, 15, 25)]
+    W = oracle.World(sc, synth.params(pgs_iters=30))
+    W.set_protocol(synth._protocol([moves], 1))
+    W.run_protocol()
+    st = W.stats()
+    assert st["collapsed"][0] == 0 and st["phase"][0] == oracle.PH_DONE
+    assert st["steps"][0] == 140 and st["moves_done"][0] == 3
+    assert st["body_steps"][0] == 30 * 18 + 50 * 17 + 20 * 17 + 15 * 17 + 25 * 16
+    act = W.active()
+    assert not act[4] and not act[7] and act.sum() == 16
