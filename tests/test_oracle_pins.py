@@ -992,3 +992,35 @@ def test_schedule_counts_steps_moves_and_body_steps_by_definition():
     assert st["body_steps"][0] == 30 * 18 + 50 * 17 + 20 * 17 + 15 * 17 + 25 * 16
     act = W.active()
     assert not act[4] and not act[7] and act.sum() == 16
+
+
+def test_schedule_collapse_then_rest_phase_by_definition():
+    # block 0 sits on the ground and is the pushed block (no force, so it is
+    # left out of the collapse terms while pushed); block 1 is thrown from
+    # 1 m up at 20 m/s, spinning at 200 rad/s: after one step it has moved
+    # more than half a length, turned more than 30 deg and carries > 5e-5 J,
+    # so the episode collapses on its first step.  The rest phase then runs
+    # rest_steps steps while the block falls freely (E_k above rest_ek), or
+    # ends on its first step when rest_ek is above E_k.  Without the spin
+    # (one of the three terms missing) the schedule runs to its end.
+    hz = HALF[2]
+    blocks = [dict(half=HALF, x=(0, 0, hz), mass=0.015, mu=0.4),
+              dict(half=HALF, x=(0.5, 0, 1.0), v=(20.0, 0, 0), w=(200.0, 0, 0), mass=0.015, mu=0.4)]
+    prot = synth._protocol([[(0, synth.AXIS_Y, 1.0, 0.0, 3.0, 0, 5, 40)]], 1)
+
+    def run(spin=True, **prm):
+        bl = [dict(b) for b in blocks]
+        if not spin:
+            bl[1]["w"] = (0.0, 0.0, 0.0)
+        W = oracle.World(synth.custom_scene(bl, ground_mu=0.4), synth.params(pgs_iters=30, **prm))
+        W.set_protocol(prot)
+        W.run_protocol()
+        return W.stats()
+
+    st = run(rest_steps=10)
+    assert st["collapsed"][0] == 1 and st["resting"][0] == 0 and st["phase"][0] == oracle.PH_DONE
+    assert st["steps"][0] == 1 + 10 and st["moves_done"][0] == 0
+    st = run(rest_steps=10, rest_ek=1e3)
+    assert st["collapsed"][0] == 1 and st["resting"][0] == 1 and st["steps"][0] == 2
+    st = run(spin=False, rest_steps=10)
+    assert st["collapsed"][0] == 0 and st["steps"][0] == 5 + 40 and st["moves_done"][0] == 1
