@@ -1046,3 +1046,38 @@ def test_push_direction_and_magnitude_on_a_turned_block(axis, k, factor, body_ax
     assert v[:, 0] @ d == pytest.approx(n * H * (k * f * mu * G - mu * G), rel=1e-9)
     assert np.linalg.norm(v[:, 0] - (v[:, 0] @ d) * d) < 1e-10
     assert np.abs(w[:, 0]).max() < 1e-9
+
+
+@pytest.mark.parametrize("alpha_deg", [30.0, -50.0])
+def test_edge_edge_contact_on_skew_edges(alpha_deg):
+    # As the crossing-edge case, with B turned by alpha about z, so that its
+    # bottom edge runs at 90 deg + alpha to A's top edge (e_A . e_B = -sin
+    # alpha, not 0): both edges are horizontal, the contact normal is world z,
+    # and the closest points lie where the edges' xy projections cross,
+    # found here by a 2x2 solve.
+    alpha = math.radians(alpha_deg)
+    ext = (HALF[1] + HALF[2]) / math.sqrt(2)
+    pen = 1e-4
+    qa = qaxis((1, 0, 0), math.pi / 4)
+    qb = qmul(qaxis((0, 0, 1), alpha), qmul(qaxis((0, 1, 0), math.pi / 4), qaxis((0, 0, 1), math.pi / 2)))
+    xa = np.zeros(3)
+    xb = np.array([0.004, -0.006, 2 * ext - pen])
+    m = oracle.pair_manifold(xa, qa, HALF, xb, qb, HALF)
+    assert m["axis"] >= 6 and m["np"] == 1
+    assert np.allclose(m["n"], [0, 0, 1], atol=1e-12)
+    assert abs(m["depth"][0] - pen) < 1e-12
+
+    def corners(x, q):
+        R = oracle.rotmat(q)
+        return np.array([x + R @ (np.array([sx, sy, sz]) * HALF)
+                         for sx in (-1, 1) for sy in (-1, 1) for sz in (-1, 1)])
+    ca, cb = corners(xa, qa), corners(xb, qb)
+    top_a = ca[np.isclose(ca[:, 2], ca[:, 2].max())]
+    bot_b = cb[np.isclose(cb[:, 2], cb[:, 2].min())]
+    assert len(top_a) == 2 and len(bot_b) == 2
+    da, db = top_a[1] - top_a[0], bot_b[1] - bot_b[0]
+    assert abs(da[:2] @ db[:2] / np.linalg.norm(da) / np.linalg.norm(db) + math.sin(alpha)) < 1e-12
+    st = np.linalg.solve(np.array([da[:2], -db[:2]]).T, bot_b[0, :2] - top_a[0, :2])
+    assert 0 < st[0] < 1 and 0 < st[1] < 1                  # the crossing lies on both edges
+    exp = np.r_[top_a[0, :2] + st[0] * da[:2], 0.5 * (top_a[0, 2] + bot_b[0, 2])]
+    assert np.allclose(m["p"][0], exp, atol=1e-12)
