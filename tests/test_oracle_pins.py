@@ -1081,3 +1081,30 @@ def test_edge_edge_contact_on_skew_edges(alpha_deg):
     assert 0 < st[0] < 1 and 0 < st[1] < 1                  # the crossing lies on both edges
     exp = np.r_[top_a[0, :2] + st[0] * da[:2], 0.5 * (top_a[0, 2] + bot_b[0, 2])]
     assert np.allclose(m["p"][0], exp, atol=1e-12)
+
+
+def test_face_contact_with_the_reference_face_on_b():
+    # A tilted by 0.02 rad about x sinks 1 mm into a wider slab B below it.
+    # B's face axis has the smaller overlap, by about (hy_B - hy_A) sin th =
+    # 0.55 mm, far beyond the 10 um tie band of the axis rule, so B's top
+    # face is the reference and A's bottom face the incident one: the normal
+    # points from A to B (down), and A's four bottom corners (inside B's
+    # face, so unclipped) are the points, each at its depth below B's top
+    # face, moved half of it up.
+    th, pen = 0.02, 1e-3
+    hx, hy, hz = HALF
+    slab = (0.06, 0.04, 0.0075)
+    qa = qaxis((1, 0, 0), th)
+    xa = np.array([0.0, 0.0, slab[2] + hz - pen])
+    m = oracle.pair_manifold(xa, qa, HALF, np.zeros(3), [1, 0, 0, 0], slab)
+    assert m["axis"] == 5 and m["np"] == 4
+    assert np.allclose(m["n"], [0, 0, -1], atol=1e-15)
+    R = rodrigues((1, 0, 0), th)
+    bottom = np.array([xa + R @ np.array([sx * hx, sy * hy, -hz]) for sx in (-1, 1) for sy in (-1, 1)])
+    depth = slab[2] - bottom[:, 2]
+    assert depth.min() > 0 and np.all(np.abs(bottom[:, :2]) < slab[:2])
+    exp = bottom + np.outer(depth / 2, [0, 0, 1])
+    dist = np.linalg.norm(m["p"][:4, None, :] - exp[None, :, :], axis=2)
+    match = dist.argmin(axis=1)
+    assert sorted(match) == [0, 1, 2, 3] and dist.min(axis=1).max() < 1e-12
+    assert np.allclose(m["depth"][:4], depth[match], atol=1e-13)
