@@ -1108,3 +1108,31 @@ def test_face_contact_with_the_reference_face_on_b():
     match = dist.argmin(axis=1)
     assert sorted(match) == [0, 1, 2, 3] and dist.min(axis=1).max() < 1e-12
     assert np.allclose(m["depth"][:4], depth[match], atol=1e-13)
+
+
+@pytest.mark.parametrize("m_low,m_high", [(0.015, 0.045), (0.045, 0.015)])
+def test_baumgarte_split_follows_inverse_mass(m_low, m_high):
+    # Eq. baumgarte with unequal masses (1:3, either way up): the correction
+    # beta (depth - slop) is shared in proportion to the inverse masses, so
+    # the lighter block moves 3/4 of it and the heavier 1/4, apart along the
+    # normal, and the pair's centre of mass does not move.  (With equal
+    # masses, a swap of the two shares cannot be seen.)
+    beta, slop, d = 0.35, 4e-4, 2e-3
+    hz = HALF[2]
+    sc = synth.custom_scene([dict(half=HALF, x=(0, 0, 1.0), mass=m_low, mu=0.4),
+                             dict(half=HALF, x=(0, 0, 1.0 + 2 * hz - d), mass=m_high, mu=0.4)], ground_mu=0.4)
+    for k in ("half", "x", "q", "v", "w", "mass", "mu", "ground_mu"):
+        setattr(sc, k, getattr(sc, k).astype(float))
+    sc.half[:, :] = np.array(HALF)[:, None]
+    sc.mass[:] = (m_low, m_high)
+    sc.x[:, 0] = (0, 0, 1.0); sc.x[:, 1] = (0, 0, 1.0 + 2 * hz - d)
+    W = oracle.World(sc, synth.params(residual_tol=1e-12, pgs_iter_cap=200000, gravity=(0.0, 0.0, 0.0)))
+    W.step(1)
+    x = W.state()[0]
+    corr = beta * (d - slop)
+    inv = np.array([1 / m_low, 1 / m_high])
+    assert x[2, 0] == pytest.approx(1.0 - corr * inv[0] / inv.sum(), abs=1e-12)
+    assert x[2, 1] == pytest.approx(1.0 + 2 * hz - d + corr * inv[1] / inv.sum(), abs=1e-12)
+    com0 = (m_low * 1.0 + m_high * (1.0 + 2 * hz - d)) / (m_low + m_high)
+    assert (m_low * x[2, 0] + m_high * x[2, 1]) / (m_low + m_high) == pytest.approx(com0, abs=1e-12)
+    assert np.abs(x[:2]).max() < 1e-15
