@@ -1136,3 +1136,24 @@ def test_baumgarte_split_follows_inverse_mass(m_low, m_high):
     com0 = (m_low * 1.0 + m_high * (1.0 + 2 * hz - d)) / (m_low + m_high)
     assert (m_low * x[2, 0] + m_high * x[2, 1]) / (m_low + m_high) == pytest.approx(com0, abs=1e-12)
     assert np.abs(x[:2]).max() < 1e-15
+
+
+def test_tangent_basis_on_every_contact_of_a_pile():
+    # the contact frame's rule on general normals: (n, t1, n x t1) is
+    # orthonormal and right-handed; t1 lies in the plane of n and the
+    # reference axis e (world X, or world Y where |n . X| > 0.9) and points
+    # along e.  Both branches occur on the pile (ground and side contacts).
+    sc = synth.pile_scene(n_boxes=24, seed=7, spread=0.05, height=0.03)
+    W = oracle.World(sc, synth.params())
+    W.step(1)
+    C = oracle.contact_dicts(W.contacts(0))
+    branches = set()
+    for c in C:
+        n, t1 = c["n"], c["t1"]
+        t2 = np.cross(n, t1)
+        F = np.array([n, t1, t2])
+        assert np.allclose(F @ F.T, np.eye(3), atol=1e-14) and np.linalg.det(F) > 0
+        e = np.array([0.0, 1.0, 0.0]) if abs(n[0]) > 0.9 else np.array([1.0, 0.0, 0.0])
+        branches.add(int(e[1]))
+        assert abs(t1 @ np.cross(n, e)) < 1e-14 and t1 @ e > 0
+    assert branches == {0, 1}
