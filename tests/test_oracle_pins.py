@@ -1157,3 +1157,24 @@ def test_tangent_basis_on_every_contact_of_a_pile():
         branches.add(int(e[1]))
         assert abs(t1 @ np.cross(n, e)) < 1e-14 and t1 @ e > 0
     assert branches == {0, 1}
+
+
+def test_removed_block_leaves_detection_and_integration():
+    # Sec. 5 removal: the middle block of level 1 is taken out of a 3-level
+    # tower.  It appears in no contact from then on, its pose and velocity
+    # stay as they were (no gravity, no integration), and it no longer
+    # counts among the dynamic bodies of a step.
+    sc = synth.build_scene([synth.Tower(levels=3, mu=0.4)], 0)
+    W = oracle.World(sc, synth.params(pgs_iters=30))
+    W.step(2)
+    assert any(4 in (int(c[0]), int(c[1])) for c in W.contacts(0))
+    x0, q0, v0, w0 = W.state()
+    bs0 = W.stats()["body_steps"][0]
+    assert W.remove_block(0, 4) == 0
+    W.step(3)
+    assert not any(4 in (int(c[0]), int(c[1])) for c in W.contacts(0))
+    x1, q1, v1, w1 = W.state()
+    for a0, a1 in ((x0, x1), (q0, q1), (v0, v1), (w0, w1)):
+        assert np.array_equal(a0[:, 4], a1[:, 4])
+    assert not W.active()[4]
+    assert W.stats()["body_steps"][0] - bs0 == 3 * 8
