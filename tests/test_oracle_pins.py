@@ -1178,3 +1178,20 @@ def test_removed_block_leaves_detection_and_integration():
         assert np.array_equal(a0[:, 4], a1[:, 4])
     assert not W.active()[4]
     assert W.stats()["body_steps"][0] - bs0 == 3 * 8
+
+
+def test_free_fall_with_substeps_closed_form():
+    # n_sub = 3 (the paper's value): a step is three substeps of h = dt / 3,
+    # so after n steps the semi-implicit closed form holds with 3n substeps of
+    # h; a step counts once in the step and body-step counters.
+    n, ns = 37, 3
+    hs = H / ns
+    W = one_box_world((0.1, -0.2, 2.0), v=(0.3, 0.0, 0.0), n_sub=ns)
+    W.step(n)
+    x, _, v, _ = W.state()
+    k = n * ns
+    assert abs(v[2, 0] - (-G * k * hs)) < 1e-12
+    assert abs(x[2, 0] - (2.0 - G * hs * hs * k * (k + 1) / 2)) < 1e-12
+    assert abs(x[0, 0] - (0.1 + 0.3 * n * H)) < 1e-12
+    st = W.stats()
+    assert st["steps"][0] == n and st["body_steps"][0] == n
