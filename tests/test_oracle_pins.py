@@ -1026,17 +1026,19 @@ def test_schedule_collapse_then_rest_phase_by_definition():
     assert st["collapsed"][0] == 0 and st["steps"][0] == 5 + 40 and st["moves_done"][0] == 1
 
 
+@pytest.mark.parametrize("n_sub", [1, 3])
 @pytest.mark.parametrize("axis,k,factor,body_axis", [("AXIS_X", 4.0, 0.5, 1), ("AXIS_Y", 3.0, 2.0 / 3.0, 0)])
-def test_push_direction_and_magnitude_on_a_turned_block(axis, k, factor, body_axis):
+def test_push_direction_and_magnitude_on_a_turned_block(axis, k, factor, body_axis, n_sub):
     # Sec. 5: the push on block X acts along the block's width (body y), on
     # block Y along its length (body x), with F = factor k mu_s m g at the COM.
     # A lone block turned 30 deg about z, pushed at F = 2 mu_s m g for 20 steps
     # with the Coulomb cone (which keeps a slide's direction): it slides from
     # the first step and gains h (F/m - mu_s g) = h mu_s g per step along the
-    # push axis, with no sideways or vertical speed.
+    # push axis, with no sideways or vertical speed.  With substeps the push
+    # acts in every substep of its steps, so the gain per step is the same.
     mu, yaw, n = 0.4, math.radians(30.0), 20
     W = one_box_world((0, 0, HALF[2]), q=qaxis((0, 0, 1), yaw), mu=mu, friction_cone=1,
-                      residual_tol=1e-12, pgs_iter_cap=100000)
+                      residual_tol=1e-12, pgs_iter_cap=100000, n_sub=n_sub)
     W.set_protocol(synth._protocol([[(0, getattr(synth, axis), 1.0, factor, k, 0, n, 0)]], 1))
     W.run_protocol()
     assert W.stats()["steps"][0] == n
