@@ -123,3 +123,49 @@ def test_warm_start_match_radius():
         assert np.all(second[second[:, 22] == 0, 19:22] == 0)
         if n_matched == 4:
             assert abs(second[:, 19].sum() - 0.015 / 0.015) < 1e-6   # previous total normal impulse m g h
+
+
+def test_recorder_features_of_a_moving_spinning_pair():
+    """The A28 features of a block-on-block pair in the air, both moving and
+    spinning, masses 2:1: per point, the relative velocity
+    (v_B + w_B x r_B) - (v_A + w_A x r_A) after the gravity predictor, in
+    the contact frame, over g h; then depth / margin, n, t1, the scaled
+    inverse masses and inertias of A and B in that order, mu, zero
+    impulses, and the unmatched and not-ground flags."""
+    hx, hy, hz = 0.0375, 0.0125, 0.0075
+    mA, mB, mu, pen = 0.030, 0.015, 0.4, 1e-4
+    vA, wA = np.array([0.1, -0.05, 0.02]), np.array([0.5, -0.3, 0.8])
+    vB, wB = np.array([-0.07, 0.12, -0.03]), np.array([-0.4, 0.6, 0.2])
+    xA, xB = np.array([0.0, 0.0, 1.0]), np.array([0.01, 0.0, 1.0 + 2 * hz - pen])
+    sc = synth.custom_scene([dict(half=(hx, hy, hz), x=tuple(xA), v=tuple(vA), w=tuple(wA), mass=mA, mu=mu),
+                             dict(half=(hx, hy, hz), x=tuple(xB), v=tuple(vB), w=tuple(wB), mass=mB, mu=mu)],
+                            ground_mu=mu)
+    for k in ("half", "x", "q", "v", "w", "mass", "mu", "ground_mu"):
+        setattr(sc, k, getattr(sc, k).astype(float))
+    sc.half[:, :] = np.array([hx, hy, hz])[:, None]
+    sc.x[:, 0], sc.x[:, 1] = xA, xB
+    sc.v[:, 0], sc.v[:, 1], sc.w[:, 0], sc.w[:, 1] = vA, vB, wA, wB
+    sc.mass[:] = (mA, mB); sc.mu[:] = mu
+    prm = synth.params(residual_tol=1e-10, pgs_iter_cap=20000)
+    W = oracle.World(sc, prm)
+    W.set_recorder(64, 1)
+    W.step(1)
+    rows = W.recorded()
+    C = oracle.contact_dicts(W.contacts(0))
+    assert len(C) == 1 and (C[0]["a"], C[0]["b"]) == (0, 1) and C[0]["np"] == 4 and len(rows) == 4
+    c = C[0]
+    gh = 9.81 / 240.0
+    g = np.array([0.0, 0.0, -9.81]) / 240.0            # the predictor's h g
+    n, t1 = c["n"], c["t1"]
+    t2 = np.cross(n, t1)
+    scale_I = 1.0 / (0.015 * 0.075 ** 2)
+    I_box = lambda m: m / 3.0 * np.array([hy * hy + hz * hz, hx * hx + hz * hz, hx * hx + hy * hy])
+    for r, p, d in zip(rows, c["p"], c["depth"]):
+        u = (vB + g + np.cross(wB, p - xB)) - (vA + g + np.cross(wA, p - xA))
+        assert np.allclose(r[0:3] * gh, [u @ n, u @ t1, u @ t2], atol=1e-13)
+        assert abs(r[3] - d / prm["contact_margin"]) < 1e-12
+        assert np.allclose(r[4:7], n) and np.allclose(r[7:10], t1)
+        assert abs(r[10] - 0.015 / mA) < 1e-12 and abs(r[11] - 0.015 / mB) < 1e-12
+        assert np.allclose(r[12:15], I_box(mA) * scale_I, rtol=1e-12)
+        assert np.allclose(r[15:18], I_box(mB) * scale_I, rtol=1e-12)
+        assert abs(r[18] - mu) < 1e-12 and np.all(r[19:23] == 0) and r[23] == 0
