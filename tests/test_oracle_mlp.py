@@ -169,3 +169,39 @@ def test_recorder_features_of_a_moving_spinning_pair():
         assert np.allclose(r[12:15], I_box(mA) * scale_I, rtol=1e-12)
         assert np.allclose(r[15:18], I_box(mB) * scale_I, rtol=1e-12)
         assert abs(r[18] - mu) < 1e-12 and np.all(r[19:23] == 0) and r[23] == 0
+
+
+def test_warm_start_match_follows_body_a():
+    """Warm-start matching compares points in body A's coordinates: the same
+    block-on-block pair, moved rigidly as a whole between steps (turned 20 deg
+    about z and shifted 5 cm), keeps all four points' impulses although every
+    point moved by more than the 2 mm radius in world coordinates."""
+    hx, hy, hz = 0.0375, 0.0125, 0.0075
+    sc = synth.custom_scene([dict(half=(hx, hy, hz), x=(0, 0, hz), mass=0.0, mu=0.4),
+                             dict(half=(hx, hy, hz), x=(0, 0, 3 * hz), mass=0.015, mu=0.4)], ground_mu=0.4)
+    for k in ("half", "x", "q", "v", "w", "mass", "mu", "ground_mu"):
+        setattr(sc, k, getattr(sc, k).astype(float))
+    sc.half[:, :] = np.array([hx, hy, hz])[:, None]
+    sc.x[:, 0] = (0, 0, hz); sc.x[:, 1] = (0, 0, 3 * hz); sc.mass[:] = (0.0, 0.015)
+    W = oracle.World(sc, synth.params(residual_tol=1e-10, pgs_iter_cap=20000))
+    W.set_recorder(64, 1)
+    W.step(1)
+    p1 = oracle.contact_dicts(W.contacts(0))[0]["p"]
+    x, q, v, w = (a.copy() for a in W.state())
+    ang, shift = np.radians(20.0), np.array([0.05, 0.02, 0.0])
+    Rz = np.array([[np.cos(ang), -np.sin(ang), 0], [np.sin(ang), np.cos(ang), 0], [0, 0, 1]])
+    qz = np.array([np.cos(ang / 2), 0, 0, np.sin(ang / 2)])
+    for j in range(2):
+        x[:, j] = Rz @ x[:, j] + shift
+        a, b = qz, q[:, j]                      # q <- qz (x) q
+        q[:, j] = [a[0] * b[0] - a[3] * b[3], a[0] * b[1] - a[3] * b[2],
+                   a[0] * b[2] + a[3] * b[1], a[0] * b[3] + a[3] * b[0]]
+    W.set_state(x, q, np.zeros_like(v), np.zeros_like(w))
+    W.step(1)
+    c2 = oracle.contact_dicts(W.contacts(0))
+    assert len(c2) == 1 and c2[0]["np"] == 4
+    moved = np.linalg.norm(c2[0]["p"][:, None, :] - p1[None, :, :], axis=2).min(axis=1)
+    assert moved.min() > 0.01                   # far beyond the match radius in world terms
+    second = W.recorded()[4:8]
+    assert np.all(second[:, 22] == 1)
+    assert abs(second[:, 19].sum() - 1.0) < 1e-6   # the previous total normal impulse m g h
