@@ -1244,9 +1244,11 @@ int or_get_contacts(const or_world* W, int e, double* out, int cap) {
 }
 
 /* Eq. stability: support polygon = convex hull (Andrew's monotone chain) of
-   the xy corners of ground-touching blocks; d = min signed distance from the
-   COM to the hull edges, positive inside.  Reading for degenerate hulls
-   (fewer than 3 vertices): minus the distance to the segment or point. */
+   the xy corners of ground-touching blocks; d = min over the hull edges of
+   the signed distance from the COM to the edge's line, positive inside
+   (reading: inside, that is the distance to the boundary; outside, it is not
+   the distance to the polygon).  Reading for degenerate hulls (fewer than 3
+   vertices): minus the distance to the segment or point. */
 static int cmp_xy(const void* a, const void* b) {
   const double *p = (const double*)a, *q = (const double*)b;
   if (p[0] != q[0]) return p[0] < q[0] ? -1 : 1;

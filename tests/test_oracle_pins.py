@@ -1197,3 +1197,32 @@ def test_free_fall_with_substeps_closed_form():
     assert abs(x[0, 0] - (0.1 + 0.3 * n * H)) < 1e-12
     st = W.stats()
     assert st["steps"][0] == n and st["body_steps"][0] == n
+
+
+def test_support_margin_on_a_turned_rectangle():
+    # Eq. stability on a 4 x 2 rectangle turned by 30 deg (edges off the
+    # axes), with interior points and duplicates among the inputs.  Inside,
+    # the margin is the distance to the boundary, found here by brute force
+    # over the four edge segments.  Outside, beyond a corner, the reading
+    # (the smallest signed distance to the edges' lines) gives minus the
+    # larger of the two line distances, not minus the distance to the corner.
+    c, s = math.cos(math.radians(30)), math.sin(math.radians(30))
+    R = np.array([[c, -s], [s, c]])
+    corners = np.array([[-2, -1], [2, -1], [2, 1], [-2, 1]], float) @ R.T + [0.3, -0.2]
+    inner = np.array([[0, 0], [1, 0.5], [-1.5, 0.2]], float) @ R.T + [0.3, -0.2]
+    pts = np.vstack([corners, inner, corners[:2]])
+
+    def seg_dist(p, a, b):
+        t = np.clip((p - a) @ (b - a) / ((b - a) @ (b - a)), 0, 1)
+        return np.linalg.norm(p - (a + t * (b - a)))
+
+    rng = np.random.default_rng(5)
+    for _ in range(200):
+        local = rng.uniform([-2, -1], [2, 1])
+        p = local @ R.T + [0.3, -0.2]
+        exp = min(seg_dist(p, corners[i], corners[(i + 1) % 4]) for i in range(4))
+        assert oracle.support_margin(pts, p) == pytest.approx(exp, abs=1e-12)
+    # beyond the (+2, +1) corner by (0.5, 0.3) in the rectangle's frame: the
+    # lines x = 2 and y = 1 are 0.5 and 0.3 away, the corner sqrt(0.34)
+    p = np.array([2.5, 1.3]) @ R.T + [0.3, -0.2]
+    assert oracle.support_margin(pts, p) == pytest.approx(-0.5, abs=1e-12)
