@@ -1226,3 +1226,68 @@ def test_support_margin_on_a_turned_rectangle():
     # lines x = 2 and y = 1 are 0.5 and 0.3 away, the corner sqrt(0.34)
     p = np.array([2.5, 1.3]) @ R.T + [0.3, -0.2]
     assert oracle.support_margin(pts, p) == pytest.approx(-0.5, abs=1e-12)
+
+
+def test_one_row_update_uses_the_true_effective_mass():
+    # Eq. keff: with k = J M^-1 J^T (inverse effective mass, lever arm
+    # included), one Gauss-Seidel update of a lone normal row from zero
+    # brings that row's relative velocity to its target.  A block balanced
+    # on one corner (one ground point, lever arm off the normal), frictionless,
+    # e = 0, touching (bias 0), falling and spinning: after one sweep the
+    # corner's normal velocity is 0.  Wrong angular terms in k would leave
+    # it non-zero, though the converged state would not show it.
+    hx, hy, hz = HALF
+    d = np.array([hx, hy, hz]) / np.linalg.norm(HALF)
+    axis = np.cross(d, [0, 0, -1.0])              # turn the body diagonal onto -z,
+    tilt = qaxis((1, 0, 0), math.radians(15))     # then 15 deg off, so r x n != 0
+    q = qmul(tilt, qaxis(axis, math.acos(-d[2])))
+    R = rodrigues((1, 0, 0), math.radians(15)) @ rodrigues(axis, math.acos(-d[2]))
+    cz = sorted((R @ (np.array([sx, sy, sz]) * HALF))[2] for sx in (-1, 1) for sy in (-1, 1) for sz in (-1, 1))
+    low = R @ np.array([hx, hy, hz])
+    assert abs(low[2] - cz[0]) < 1e-15 and cz[1] - cz[0] > 1.2e-3  # one corner within the 1 mm margin
+    assert np.linalg.norm(np.cross(low, [0, 0, 1])) > 5e-3          # lever arm off the normal
+    x = np.array([0.01, -0.02, -low[2] - 1e-6])   # corner 1 um into the ground
+    v, w = np.array([0.2, -0.1, -0.3]), np.array([1.0, 2.0, -0.5])
+    W = one_box_world(x, q=q, v=v, w=w, mu=0.0, restitution=0.0, pgs_iters=1, residual_tol=0.0)
+    W.step(1)
+    C = oracle.contact_dicts(W.contacts(0))
+    assert len(C) == 1 and C[0]["a"] == -1 and C[0]["np"] == 1
+    p = C[0]["p"][0]
+    r = p - x
+    u_pre = (v + H * np.array([0, 0, -G])) + np.cross(w, r)
+    assert u_pre[2] < -0.1                        # approaching
+    _, _, v1, w1 = W.state()
+    u = v1[:, 0] + np.cross(w1[:, 0], r)
+    assert abs(u[2]) < 1e-13
+    assert C[0]["lam"][0, 0] > 0 and np.all(C[0]["lam"][0, 1:] == 0)
+
+
+def test_one_row_update_between_two_spinning_blocks():
+    # The same one-sweep property on a single edge-edge point between two
+    # free blocks in the air (masses 1:2, both moving and spinning), so that
+    # both bodies' angular terms of k count.  Gravity moves both alike.
+    ext = (HALF[1] + HALF[2]) / math.sqrt(2)
+    qa = qaxis((1, 0, 0), math.pi / 4)
+    qb = qmul(qaxis((0, 0, 1), math.radians(30)), qmul(qaxis((0, 1, 0), math.pi / 4), qaxis((0, 0, 1), math.pi / 2)))
+    xa = np.array([0.0, 0.0, 1.0])
+    xb = xa + np.array([0.004, -0.006, 2 * ext - 1e-6])
+    vA, wA = np.array([0.05, 0.1, 0.2]), np.array([0.7, -1.2, 0.4])
+    vB, wB = np.array([-0.1, 0.03, -0.25]), np.array([-0.9, 0.5, 1.3])
+    sc = synth.custom_scene([dict(half=HALF, x=tuple(xa), q=tuple(qa), v=tuple(vA), w=tuple(wA), mass=0.015, mu=0.0),
+                             dict(half=HALF, x=tuple(xb), q=tuple(qb), v=tuple(vB), w=tuple(wB), mass=0.030, mu=0.0)],
+                            ground_mu=0.0)
+    for k in ("half", "x", "q", "v", "w", "mass", "mu", "ground_mu"):
+        setattr(sc, k, getattr(sc, k).astype(float))
+    sc.half[:, :] = np.array(HALF)[:, None]; sc.mass[:] = (0.015, 0.030)
+    sc.x[:, 0], sc.x[:, 1], sc.q[:, 0], sc.q[:, 1] = xa, xb, qa, qb
+    sc.v[:, 0], sc.v[:, 1], sc.w[:, 0], sc.w[:, 1] = vA, vB, wA, wB
+    sc.mu[:] = 0.0
+    W = oracle.World(sc, synth.params(restitution=0.0, pgs_iters=1, residual_tol=0.0))
+    W.step(1)
+    C = oracle.contact_dicts(W.contacts(0))
+    assert len(C) == 1 and (C[0]["a"], C[0]["b"]) == (0, 1) and C[0]["np"] == 1 and C[0]["axis"] >= 6
+    p, n = C[0]["p"][0], C[0]["n"]
+    rel = lambda v, w: (v[1] + np.cross(w[1], p - xb)) - (v[0] + np.cross(w[0], p - xa))
+    assert rel((vA, vB), (wA, wB)) @ n < -0.1     # approaching
+    _, _, v1, w1 = W.state()
+    assert abs(rel(v1.T, w1.T) @ n) < 1e-13
