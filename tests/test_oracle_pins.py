@@ -1269,6 +1269,16 @@ def test_one_row_update_uses_the_true_effective_mass(mu):
         t2 = np.cross(C[0]["n"], C[0]["t1"])
         assert np.all(np.abs(lam[1:]) < mu * lam[0]) and np.all(lam[1:] != 0)
         assert abs(u @ t2) < 1e-13
+        # the residual (m/s) after that sweep: where no row's next update is
+        # clipped, k |delta lambda| = |u| per row, so it is the largest row
+        # velocity error; k from the closed-form inertia decides the clipping
+        m = 0.015
+        Iinv = R @ np.diag(3.0 / (m * np.array([hy * hy + hz * hz, hx * hx + hz * hz, hx * hx + hy * hy]))) @ R.T
+        rows = [C[0]["n"], C[0]["t1"], t2]
+        k = [1 / m + np.cross(r, e) @ Iinv @ np.cross(r, e) for e in rows]
+        un, u1 = u @ rows[0], u @ rows[1]
+        assert lam[0] - un / k[0] > 0 and abs(lam[1] - u1 / k[1]) < mu * lam[0]
+        assert W.stats()["last_residual"][0] == pytest.approx(max(abs(un), abs(u1)), abs=1e-13)
 
 
 def test_one_row_update_between_two_spinning_blocks():
