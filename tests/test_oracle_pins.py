@@ -1228,8 +1228,8 @@ def test_support_margin_on_a_turned_rectangle():
     assert oracle.support_margin(pts, p) == pytest.approx(-0.5, abs=1e-12)
 
 
-@pytest.mark.parametrize("mu", [0.0, 5.0])
-def test_one_row_update_uses_the_true_effective_mass(mu):
+@pytest.mark.parametrize("mu,e", [(0.0, 0.0), (5.0, 0.0), (0.0, 0.1)])
+def test_one_row_update_uses_the_true_effective_mass(mu, e):
     # Eq. keff: with k = J M^-1 J^T (inverse effective mass, lever arm
     # included), one Gauss-Seidel update of a lone normal row from zero
     # brings that row's relative velocity to its target.  A block balanced
@@ -1238,7 +1238,9 @@ def test_one_row_update_uses_the_true_effective_mass(mu):
     # corner's normal velocity is 0.  Wrong angular terms in k would leave
     # it non-zero, though the converged state would not show it.  With a
     # friction limit that does not clip (mu = 5), the sweep's last row, t2,
-    # is the one left exactly on target (u_t2 = 0), which pins k_t2.
+    # is the one left exactly on target (u_t2 = 0), which pins k_t2.  With
+    # e = 0.1 the row carries the listing's (1 + e) factor and overshoots to
+    # u_n = -e u_n(before).
     hx, hy, hz = HALF
     d = np.array([hx, hy, hz]) / np.linalg.norm(HALF)
     axis = np.cross(d, [0, 0, -1.0])              # turn the body diagonal onto -z,
@@ -1251,7 +1253,7 @@ def test_one_row_update_uses_the_true_effective_mass(mu):
     assert np.linalg.norm(np.cross(low, [0, 0, 1])) > 5e-3          # lever arm off the normal
     x = np.array([0.01, -0.02, -low[2] - 1e-6])   # corner 1 um into the ground
     v, w = np.array([0.2, -0.1, -0.3]), np.array([1.0, 2.0, -0.5])
-    W = one_box_world(x, q=q, v=v, w=w, mu=mu, restitution=0.0, pgs_iters=1, residual_tol=0.0)
+    W = one_box_world(x, q=q, v=v, w=w, mu=mu, restitution=e, pgs_iters=1, residual_tol=0.0)
     W.step(1)
     C = oracle.contact_dicts(W.contacts(0))
     assert len(C) == 1 and C[0]["a"] == -1 and C[0]["np"] == 1
@@ -1264,7 +1266,7 @@ def test_one_row_update_uses_the_true_effective_mass(mu):
     lam = C[0]["lam"][0]
     assert lam[0] > 0
     if mu == 0.0:
-        assert abs(u[2]) < 1e-13 and np.all(lam[1:] == 0)
+        assert abs(u[2] + e * u_pre[2]) < 1e-13 and np.all(lam[1:] == 0)
     else:
         t2 = np.cross(C[0]["n"], C[0]["t1"])
         assert np.all(np.abs(lam[1:]) < mu * lam[0]) and np.all(lam[1:] != 0)
