@@ -13,6 +13,13 @@
  * Units SI, z up, quaternions q = [w, x, y, z] (Hamilton), angular velocity in
  * the world frame.  Arrays crossing this header are structure-of-arrays,
  * component-major: x[c * B + b].
+ *
+ * Every step function is pinned by the tests to closed forms, brute force,
+ * invariants or the paper's printed thresholds.  Parity unpinned: whole
+ * collapse episodes (or_run_protocol over a push/removal schedule that ends
+ * in a collapse) are chaotic; their outcomes are compared only statistically.
+ * The X-axis Ziglar factor k = 4 enters only as a schedule input, pinned to
+ * the paper's printed force and not to a derivation.
  */
 #ifndef JB_ORACLE_H
 #define JB_ORACLE_H
