@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--episodes", type=int, default=0, help="use the first n episodes (0 = all 450)")
     ap.add_argument("--max-steps", type=int, default=1 << 30, help="cap physics steps per episode")
     ap.add_argument("--tol", type=float, default=1e-5)
+    ap.add_argument("--accel", type=int, default=64,
+                    help="PGS acceleration: a nonsmooth conjugate-gradient step every this many sweeps (0 = plain PGS)")
     ap.add_argument("--cap", type=int, default=20000)
     ap.add_argument("--fixed-iters", type=int, default=0,
                     help="fixed-sweep mode with this many sweeps per solve (profiling)")
@@ -108,7 +110,8 @@ def workload(args, rank):
         E = scene.n_episodes
         idx = np.linspace(0, E - 1, args.episodes).round().astype(int)
         scene, prot = synth.subset(scene, prot, idx)
-    prm = dict(prm, residual_tol=args.tol, pgs_iter_cap=args.cap, stall_window=getattr(args, "stall_window", 0))
+    prm = dict(prm, residual_tol=args.tol, pgs_iter_cap=args.cap, stall_window=getattr(args, "stall_window", 0),
+               pgs_accel_period=getattr(args, "accel", 0))
     if args.fixed_iters:
         prm = dict(prm, residual_tol=0.0, pgs_iters=args.fixed_iters)
     return scene, prot, prm

@@ -128,6 +128,16 @@ typedef struct {
                                rows without the factor and a touching point approaching faster
                                than restitution_vmin targets v_n = -e v_n(pre-solve) */
   float restitution_vmin;   /* m/s; <= 0 selects 2 |g| h (resting contacts approach at |g| h) */
+  int32_t pgs_accel_period; /* 0: plain projected Gauss-Seidel (the paper).  m > 0: after every m
+                               sweeps of a solve, one nonsmooth conjugate-gradient step
+                               (Silcowitz, Niebe and Erleben 2010, with a block of m sweeps as
+                               the map G): r = G(lambda) - lambda over the block, beta =
+                               |r_k|^2 / |r_(k-1)|^2 (0 on the first block and when above 1),
+                               lambda <- proj(G(lambda) + beta d), d <- r_k + beta d, the
+                               impulse change applied to the bodies.  A fixed point of the sweep
+                               is one of this iteration, so the converged impulses are plain
+                               PGS's and the residual test is unchanged; the sweeps needed to
+                               reach residual_tol fall.  Uses jb_workspace_bytes' scratch. */
 } jb_solver_params;
 
 /* Initial scene: host arrays, B = body_off[n_episodes] bodies. */
@@ -250,13 +260,26 @@ jb_status jb_set_protocol(jb_batch* b, const jb_protocol* prot);
  * steps in one persistent launch.  Asynchronous. */
 jb_status jb_run_protocol(jb_batch* b, int32_t max_steps);
 
-/* Host-driven stepping.  jb_apply_push: for n entries, constant force
- * force_N (signed) along the block's axis (direction fixed at the call) for
- * n_steps steps.  jb_remove_block deactivates blocks.  jb_step advances all
- * episodes in the host-driven phase by n_steps steps.  Asynchronous. */
+/* Host-driven stepping.  Asynchronous; argument errors (null arrays, n < 0,
+ * episode or block out of range: JB_EINVAL / JB_ERANGE) are returned before
+ * anything is queued.  Host arrays are read during the call only.
+ *
+ * jb_apply_push (Sec. 5, Eq. 4 and Eq. 8: a push of F_app along one of the
+ * block's own axes, at its centre of mass; the caller picks F_app, e.g.
+ * k mu_s m g): for n entries, a constant force force_N (signed, N) along
+ * the block's axis (JB_AXIS_X = width axis, JB_AXIS_Y = long axis; the
+ * direction is fixed at the call) for n_steps steps. */
 jb_status jb_apply_push(jb_batch* b, int32_t n, const int32_t* episode, const int32_t* block,
                         const int32_t* axis, const float* force_N, const int32_t* n_steps);
+/* jb_remove_block (the removal rounds of Sec. 12.2 and Sec. 13.1: a block
+ * taken out of the tower): deactivates n blocks; they leave the broadphase,
+ * their contacts and warm-start entries, and the body-step count, and keep
+ * their last pose. */
 jb_status jb_remove_block(jb_batch* b, int32_t n, const int32_t* episode, const int32_t* block);
+/* jb_step (Sec. 4.2 and Sec. 6-7: forces and the velocity predictor, AABB
+ * broadphase, SAT narrowphase and manifold, PGS, integration, Baumgarte
+ * correction, n_sub substeps per step): advances every episode in the
+ * host-driven phase by n_steps steps. */
 jb_status jb_step(jb_batch* b, int32_t n_steps);
 
 /* Waits for queued work; *n_bad_episodes (may be NULL) = episodes whose status is non-zero. */
@@ -270,8 +293,10 @@ jb_status jb_sync(jb_batch* b, int32_t* n_bad_episodes);
 jb_status jb_size_classes(const jb_batch* b, int32_t* n_classes, int32_t* episodes, int32_t* max_bodies,
                           int32_t* grid);
 
-/* State transfer, [3][B] / [4][B] arrays, host pointers unless device_ptrs != 0
- * (then device pointers, copied on the batch stream).  Any pointer may be NULL.
+/* State transfer (Sec. 4.1: the state S = (x, q, v, w) of every body),
+ * [3][B] / [4][B] arrays, host pointers unless device_ptrs != 0 (then device
+ * pointers, copied on the batch stream).  Any pointer may be NULL.  Host
+ * reads synchronise the batch stream; a NULL batch gives JB_EINVAL.
  * jb_write_state keeps the contact cache unless clear_cache != 0 and, when
  * reset_reference != 0, takes the new poses as the collapse reference. */
 jb_status jb_read_state(jb_batch* b, float* x, float* q, float* v, float* w, int32_t device_ptrs);
@@ -281,11 +306,19 @@ jb_status jb_write_state(jb_batch* b, const float* x, const float* q, const floa
 /* Active flags [B] (1 = in the simulation). */
 jb_status jb_read_active(jb_batch* b, int32_t* active);
 
-/* Contact points of the last substep of one episode, natural order (ground
- * pairs by body, then pairs (a, b) ascending, points in manifold order). */
+/* Contact points of the last substep of one episode (Sec. 6.2.1: the
+ * clipped manifold of each pair, at most 4 points, with the impulses of the
+ * Sec. 7 solve), natural order (ground pairs by body, then pairs (a, b)
+ * ascending, points in manifold order).  out is a host array of cap entries;
+ * *n_out = points written.  JB_ERANGE for a bad episode; JB_ENOMEM if the
+ * episode has more than cap points (the first cap are written).
+ * Synchronises the batch stream. */
 jb_status jb_read_contacts(jb_batch* b, int32_t episode, jb_contact* out, int32_t cap,
                            int32_t* n_out);
-/* Per-episode statistics [E]; computes the support-polygon margin on the device. */
+/* Per-episode statistics [E] (host array; Sec. 8: the support-polygon margin
+ * of Eq. stability as com_imbalance = -margin, the Eq. collapse flag and
+ * fallen count, the Sec. 8.3 rest test; plus solver counters).  Computes the
+ * margin on the device and synchronises the batch stream. */
 jb_status jb_read_episode_stats(jb_batch* b, jb_episode_stats* out);
 
 /* Reference-episode search (Sec. 11.2, the similarity step): among the
@@ -296,8 +329,11 @@ jb_status jb_read_episode_stats(jb_batch* b, jb_episode_stats* out);
  * Synchronous: reads the episode statistics and the active flags. */
 jb_status jb_reference_episode(jb_batch* b, int32_t n_removed_hat, int32_t* episode, int32_t* n_removed);
 
-/* Raw snapshot of all mutable device state (bodies, episode state, contact
- * caches, schedule) for exact resume.  jb_state_bytes gives the size. */
+/* Raw snapshot of all mutable device state for exact resume: the Sec. 4.1
+ * state of every body, the episode schedule position (Sec. 12.2 rounds), the
+ * contact caches that warm-start the Sec. 7.3 solve.  host_buf holds at least
+ * jb_state_bytes bytes (JB_ENOMEM otherwise); jb_load_state needs a snapshot
+ * of a batch of the same shape.  Both synchronise the batch stream. */
 size_t jb_state_bytes(const jb_batch* b);
 jb_status jb_save_state(jb_batch* b, void* host_buf, size_t bytes);
 jb_status jb_load_state(jb_batch* b, const void* host_buf, size_t bytes);
@@ -376,13 +412,17 @@ jb_status jb_mlp_train_step(void* d_mlp, const float* d_x, const float* d_t, int
  * the call returns without synchronising; the caller synchronises before
  * reading the outputs.
  *
+ * It runs the plain solver only: warm_start 0 or 1 (2 and 3 need a network
+ * block, which this call has no way to take: JB_EINVAL).
+ *
  * Scratch: the library's file-scope device array of JB_NOALLOC_SCRATCH_BYTES
  * (32 MiB; every GPU that loads the library holds it until the process
  * exits).  A batch whose layout needs more returns JB_ENOMEM with the sizes
  * in jb_last_error() and launches nothing.  The call makes no device memory
- * allocation and frees nothing.  Its first call on a device looks up the
- * scratch address (cudaGetSymbolAddress); make that first call before any
- * stream capture.  All calls share the one array, which keeps the last call's
+ * allocation and frees nothing.  Its first call on a device (n_steps 0
+ * included) looks up the scratch address (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  Each call also copies body_off from
+ * the caller's host memory with cudaMemcpyAsync.  All calls share the one array, which keeps the last call's
  * contents (each call re-initialises what must start at zero): calls that
  * overlap on the GPU (different streams, or different host threads) race.
  */

@@ -62,6 +62,8 @@ typedef struct {
   double lam[MAXP][3];
   int matched[MAXP];
   double feat[MAXP][OR_NFEAT];
+  double lam_start[MAXP][3];    /* acceleration: impulses at the start of the sweep block */
+  double dir[MAXP][3];          /* acceleration: conjugate direction */
 } or_pair;
 
 typedef struct {
@@ -652,8 +654,8 @@ static void sweep_order(or_episode* E, int colour) {
   if (!colour || n <= 0) return;
   int (*kv)[2] = (int(*)[2])malloc(sizeof(int) * 2 * (size_t)n);
   for (int i = 0; i < n; ++i) {
-    kv[i][0] = (int)floor((E->pairs[i].p[0][2] + 5e-4) * 1000.0) + 1;   /* 1 mm height bin */
-    kv[i][1] = -i;                                                    /* then index descending */
+    kv[i][0] = ((E->pairs[i].a + 1) << 16) | (0xffff - E->pairs[i].b);   /* a ascending, b descending */
+    kv[i][1] = -i;
   }
   qsort(kv, n, sizeof(int) * 2, cmp_int2);
   unsigned long long* used = (unsigned long long*)calloc(E->nb + 1, sizeof(unsigned long long));
@@ -756,14 +758,88 @@ static double pgs_residual(or_episode* E, int cone) {
   return r;
 }
 
+/* Optional acceleration of the sweeps (not in the paper): the nonsmooth
+   nonlinear conjugate gradient method of Silcowitz, Niebe and Erleben ("A
+   nonsmooth nonlinear conjugate gradient method for interactive contact force
+   problems", The Visual Computer, 2010), with one conjugate-gradient step per
+   block of m sweeps instead of per sweep.  Treating a block of sweeps as the
+   map lambda -> G(lambda), with r = G(lambda) - lambda the change over the
+   block:
+     beta = |r_k|^2 / |r_(k-1)|^2 (Fletcher-Reeves; beta = 0 for the first
+            block and whenever beta > 1, the restart),
+     lambda <- proj(G(lambda) + beta d),   d <- r_k + beta d,
+   where proj is each row's own projection (lambda_n >= 0, then the friction
+   limits with the new lambda_n; the disc with the cone).  Reading: the step is
+   projected so that the state stays feasible.  The impulse change of the step
+   is applied to the bodies like any other impulse.  A fixed point of the
+   sweep has r = 0, so it is a fixed point of this iteration and the converged
+   impulses are plain PGS's; only the sweeps needed to reach a tolerance
+   change.  These helpers run over the pairs in sweep order. */
+static void accel_begin(or_episode* E) {
+  for (int c = 0; c < E->np; ++c) {
+    or_pair* pr = &E->pairs[c];
+    for (int i = 0; i < pr->np; ++i)
+      for (int k = 0; k < 3; ++k) { pr->lam_start[i][k] = pr->lam[i][k]; pr->dir[i][k] = 0; }
+  }
+}
+
+static double accel_change2(const or_episode* E) {
+  double s = 0;
+  for (int c = 0; c < E->np; ++c) {
+    const or_pair* pr = &E->pairs[c];
+    for (int i = 0; i < pr->np; ++i)
+      for (int k = 0; k < 3; ++k) { double r = pr->lam[i][k] - pr->lam_start[i][k]; s += r * r; }
+  }
+  return s;
+}
+
+static void accel_step(or_episode* E, double beta, int cone) {
+  for (int cc = 0; cc < E->np; ++cc) {
+    or_pair* pr = &E->pairs[E->order[cc]];
+    or_body *A = body_ref(E, pr->a), *B = body_ref(E, pr->b);
+    for (int i = 0; i < pr->np; ++i) {
+      double nl[3];
+      for (int k = 0; k < 3; ++k) nl[k] = pr->lam[i][k] + beta * pr->dir[i][k];
+      nl[0] = fmax(0.0, nl[0]);
+      const double lim = pr->mu * nl[0];
+      if (cone) disc_project(nl[1], nl[2], lim, &nl[1], &nl[2]);
+      else { nl[1] = clampd(nl[1], -lim, lim); nl[2] = clampd(nl[2], -lim, lim); }
+      double Pv[3] = {0, 0, 0};
+      for (int k = 0; k < 3; ++k) {
+        const double dl = nl[k] - pr->lam[i][k];
+        axpy3(dl, k == 0 ? pr->n : (k == 1 ? pr->t1 : pr->t2), Pv);
+        pr->dir[i][k] = (pr->lam[i][k] - pr->lam_start[i][k]) + beta * pr->dir[i][k];
+        pr->lam[i][k] = nl[k];
+        pr->lam_start[i][k] = nl[k];
+      }
+      apply_impulse(A, B, pr->rA[i], pr->rB[i], Pv);
+    }
+  }
+}
+
+/* One sweep followed, at the end of every block of pgs_accel_period sweeps, by
+   the acceleration step.  *r2_prev carries |r|^2 of the previous block. */
+static void sweep_step(or_episode* E, const or_params* P, int sweeps_done, double* r2_prev) {
+  pgs_sweep(E, P->restitution_newton ? 0.0 : P->restitution, P->friction_cone);
+  const int m = P->pgs_accel_period;
+  if (m > 0 && (sweeps_done + 1) % m == 0) {
+    const double r2 = accel_change2(E);
+    double beta = *r2_prev > 0 ? r2 / *r2_prev : 0.0;
+    if (beta > 1.0) beta = 0.0;   /* restart */
+    *r2_prev = r2;
+    accel_step(E, beta, P->friction_cone);
+  }
+}
+
 static void solve(or_episode* E, const or_params* P) {
   sweep_order(E, P->colour_order);
   int sweeps = 0;
-  double res = 0;
+  double res = 0, r2_prev = 0;
+  if (P->pgs_accel_period > 0) accel_begin(E);
   if (E->np > 0) {
     if (P->residual_tol > 0) {
       for (;;) {
-        pgs_sweep(E, P->restitution_newton ? 0.0 : P->restitution, P->friction_cone);
+        sweep_step(E, P, sweeps, &r2_prev);
         ++sweeps;
         if (sweeps >= P->pgs_min_iters) {
           res = pgs_residual(E, P->friction_cone);
@@ -773,7 +849,7 @@ static void solve(or_episode* E, const or_params* P) {
         if (sweeps >= P->pgs_iter_cap) { E->status |= OR_STATUS_NOT_CONVERGED; break; }
       }
     } else {
-      for (int s = 0; s < P->pgs_iters; ++s) pgs_sweep(E, P->restitution_newton ? 0.0 : P->restitution, P->friction_cone);
+      for (int s = 0; s < P->pgs_iters; ++s) sweep_step(E, P, s, &r2_prev);
       sweeps = P->pgs_iters;
       res = pgs_residual(E, P->friction_cone);
     }

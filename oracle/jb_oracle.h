@@ -55,11 +55,16 @@ typedef struct {
                             targets v_n = -e v_n(pre-solve) */
   double restitution_vmin; /* m/s; <= 0 selects 2 |g| h */
   int colour_order;      /* 0: Gauss-Seidel in natural pair order (the listing); 1: in the GPU
-                            library's colour order, for comparing fixed-iteration results:
-                            greedy lowest-free colouring of the pairs taken by (contact height of
-                            their first point in 1 mm bins ascending, natural index descending),
-                            colours ascending, natural index ascending within a colour.  Static
-                            bodies (the ground) do not constrain the colouring.  Same fixed point. */
+                            library's colour order: greedy lowest-free colouring of the pairs taken
+                            by (lower body a ascending, upper body b descending), colours
+                            ascending, natural index ascending within a colour.  Static bodies
+                            (the ground) do not constrain the colouring.  Same fixed point.  This
+                            restates the GPU's schedule so that a fixed number of unconverged
+                            sweeps can be compared iterate for iterate; it is opt-in for that test
+                            alone and is never used by a pin or a converged-parity test. */
+  int pgs_accel_period;      /* 0: plain projected Gauss-Seidel (the paper).  m > 0: after every m
+                            sweeps one nonsmooth conjugate-gradient step (see solve()); the
+                            converged impulses are those of plain PGS. */
 } or_params;
 
 /* episode statistics, one row of OR_NSTAT doubles per episode */

@@ -45,7 +45,7 @@ class jb_solver_params(C.Structure):
                 ("smem_pair_factor", C.c_float), ("sor", C.c_float), ("sweep_order", C.c_int32),
                 ("residual_every_max", C.c_int32), ("stall_window", C.c_int32),
                 ("friction_cone", C.c_int32), ("restitution_newton", C.c_int32),
-                ("restitution_vmin", C.c_float)]
+                ("restitution_vmin", C.c_float), ("pgs_accel_period", C.c_int32)]
 
 
 _fp = C.POINTER(C.c_float)

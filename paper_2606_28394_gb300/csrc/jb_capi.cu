@@ -145,6 +145,7 @@ size_t carve(unsigned char* base, const Sizes& z, Dev& D, size_t* persist, int32
     c.nat_x = a.take<float>((size_t)P * kMaxPts * kFeatures);
   }
   if (persist) *persist = (a.off + 255) & ~size_t(255);
+  D.acc = a.take<float>((size_t)P * kAccFloats);
   D.work_counter = a.take<int32_t>(kMaxSizeClasses);
   int32_t* c = a.take<int32_t>(6 * (size_t)std::max(B, 1));
   jb_episode_stats* s = a.take<jb_episode_stats>(E);
@@ -200,6 +201,7 @@ Params to_params(const jb_solver_params* p) {
   q.stall_window = p->stall_window;
   q.friction_cone = p->friction_cone;
   q.restitution_newton = p->restitution_newton;
+  q.accel_period = p->pgs_accel_period;
   {
     const float g = sqrtf(p->gravity[0] * p->gravity[0] + p->gravity[1] * p->gravity[1] + p->gravity[2] * p->gravity[2]);
     q.restitution_vmin = p->restitution_vmin > 0.f ? p->restitution_vmin : 2.f * g * p->dt / (float)p->n_sub;
@@ -224,6 +226,7 @@ const char* check_params(const jb_solver_params* p) {
   if (p->stall_window < 0) return "stall_window must be >= 0";
   if (p->friction_cone < 0 || p->friction_cone > 1) return "friction_cone must be 0 or 1";
   if (p->restitution_newton < 0 || p->restitution_newton > 1) return "restitution_newton must be 0 or 1";
+  if (p->pgs_accel_period < 0) return "pgs_accel_period must be >= 0";
   return nullptr;
 }
 
@@ -820,6 +823,9 @@ jb_status jb_step_noalloc(int32_t n_episodes, const int32_t* body_off, const flo
     return fail(JB_EINVAL, "jb_step_noalloc: null argument");
   if (n_steps < 0) return fail(JB_EINVAL, "jb_step_noalloc: n_steps must be >= 0");
   if (const char* m = check_params(p)) return fail(JB_EINVAL, "jb_step_noalloc: %s", m);
+  if (p->warm_start >= 2)
+    return fail(JB_EINVAL, "jb_step_noalloc: warm_start %d needs a network block; this call runs plain PGS "
+                           "(warm_start 0 or 1)", p->warm_start);
   Sizes z;
   if (!sizes_of(n_episodes, body_off, 0, z, nullptr))
     return fail(JB_EINVAL, "jb_step_noalloc: bad n_episodes/body_off");
@@ -831,9 +837,9 @@ jb_status jb_step_noalloc(int32_t n_episodes, const int32_t* body_off, const flo
   if (need > (size_t)JB_NOALLOC_SCRATCH_BYTES)
     return fail(JB_ENOMEM, "jb_step_noalloc: this batch needs %zu bytes of scratch, the static scratch holds %u",
                 need, (unsigned)JB_NOALLOC_SCRATCH_BYTES);
-  if (n_steps == 0) return JB_OK;
   void* base = nullptr;
-  if (jb_status st = static_scratch_address(&base)) return st;
+  if (jb_status st = static_scratch_address(&base)) return st;   // first call per device: the lookup
+  if (n_steps == 0) return JB_OK;
   carve(static_cast<unsigned char*>(base), z, D, nullptr, nullptr, nullptr);
   D.E = z.E; D.B = z.B; D.nb_max = z.nb_max; D.pc_max = z.pc_max;
   D.P = to_params(p);

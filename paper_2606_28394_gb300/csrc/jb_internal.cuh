@@ -64,6 +64,7 @@ struct Params {
   int friction_cone;       // 1: disc projection of the tangent pair
   int restitution_newton;  // 1: bounce target instead of the (1+e) factor
   float restitution_vmin;  // m/s (resolved: > 0)
+  int accel_period;        // 0 = plain PGS; m > 0: a conjugate-gradient step every m sweeps
 };
 
 // One contact buffer (the batch holds two: this step's and the previous one).
@@ -85,6 +86,10 @@ struct ContactBuf {
   float* nat_x;         // [P * 4][kFeatures] warm-start features of each point
 };
 
+// Per colour-sorted slot, the acceleration state of one solve: the impulses
+// at the start of the sweep block [4][3], then the conjugate direction [4][3].
+constexpr int kAccFloats = 24;
+
 constexpr int kFeatures = 24;    // warm-start network inputs per contact point
 constexpr int kRecFloats = 27;   // recorder row: features, then converged impulses (n, t1, t2)
 // normalisation scales of the features (nominal block mass and length)
@@ -104,6 +109,7 @@ struct Dev {
   int32_t *mv_off, *mv_block, *mv_axis, *mv_remove, *mv_push, *mv_settle;
   float *mv_sign, *mv_factor, *mv_k;
   ContactBuf buf[2];
+  float* acc;             // [P][kAccFloats] per-solve acceleration state (scratch)
   int32_t* work_counter;
   const int32_t* order;   // episode processing order [E]
   Params P;

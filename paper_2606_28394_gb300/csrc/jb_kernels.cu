@@ -750,8 +750,6 @@ __device__ __forceinline__ float pair_residual(const SolverView<kS>& V, int sl, 
   }
   return r;
 }
-#undef VSP
-#undef VSF
 
 // Residual of the whole episode (warp max; NaN propagates).
 template <bool kS>
@@ -808,6 +806,142 @@ __device__ __forceinline__ void colour_passes(const SolverRef& r, const int* off
 __device__ __forceinline__ float episode_residual(const SolverRef& r, int npairs, int lane, bool cone) {
   return r.shared ? episode_residual_t<true>(r, npairs, lane, cone) : episode_residual_t<false>(r, npairs, lane, cone);
 }
+
+// ------------------------------------------------ nonsmooth CG acceleration
+// One conjugate-gradient step per block of m sweeps (Silcowitz, Niebe and
+// Erleben's nonsmooth nonlinear conjugate gradient with a block of sweeps as
+// the map G): r = G(lambda) - lambda over the block, beta = |r_k|^2 /
+// |r_(k-1)|^2 (0 on the first block and on restart, beta > 1), lambda <-
+// proj(G(lambda) + beta d), d <- r_k + beta d.  The state lives in the
+// global acc array, kAccFloats per colour-sorted slot ([4][3] impulses at
+// the block start, then [4][3] direction); unused point records are zero and
+// stay zero.  A fixed point of the sweep is one of this iteration.
+template <bool kS>
+__device__ __noinline__ void accel_begin_t(const SolverRef r, float* __restrict__ acc, int npairs, int lane) {
+  const SolverView<kS> V(r);
+  for (int sl = lane; sl < npairs; sl += 32) {
+    float4* a4 = reinterpret_cast<float4*>(acc + (size_t)sl * kAccFloats);
+    float l[12];
+#pragma unroll
+    for (int k = 0; k < kMaxPts; ++k) { l[3 * k] = VSP(10, k); l[3 * k + 1] = VSP(11, k); l[3 * k + 2] = VSP(12, k); }
+    a4[0] = make_float4(l[0], l[1], l[2], l[3]);
+    a4[1] = make_float4(l[4], l[5], l[6], l[7]);
+    a4[2] = make_float4(l[8], l[9], l[10], l[11]);
+    a4[3] = make_float4(0.f, 0.f, 0.f, 0.f);
+    a4[4] = a4[3];
+    a4[5] = a4[3];
+  }
+}
+
+// |lambda - lambda_start|^2 over the episode (warp sum).
+template <bool kS>
+__device__ __noinline__ float accel_change2_t(const SolverRef r, const float* __restrict__ acc, int npairs, int lane) {
+  const SolverView<kS> V(r);
+  float s2 = 0.f;
+  for (int sl = lane; sl < npairs; sl += 32) {
+    const float4* a4 = reinterpret_cast<const float4*>(acc + (size_t)sl * kAccFloats);
+    const float4 q0 = a4[0], q1 = a4[1], q2 = a4[2];
+    const float ls[12] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
+#pragma unroll
+    for (int k = 0; k < kMaxPts; ++k)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float d = VSP(10 + c, k) - ls[3 * k + c];
+        s2 = fmaf(d, d, s2);
+      }
+  }
+  return warp_sum(s2);
+}
+
+// The step on one pair: new impulses, direction and block start, and the
+// impulse change applied to both bodies.
+template <bool kS, bool kCone>
+__device__ __forceinline__ void accel_pair(const SolverView<kS>& V, float* __restrict__ acc, int sl, float beta) {
+  PairRegs R;
+  load_pair(V, sl, R);
+  float4* a4 = reinterpret_cast<float4*>(acc + (size_t)sl * kAccFloats);
+  float ls[12], dr[12];
+  {
+    float4 t[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) t[i] = a4[i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      ls[4 * i] = t[i].x; ls[4 * i + 1] = t[i].y; ls[4 * i + 2] = t[i].z; ls[4 * i + 3] = t[i].w;
+      dr[4 * i] = t[3 + i].x; dr[4 * i + 1] = t[3 + i].y; dr[4 * i + 2] = t[3 + i].z; dr[4 * i + 3] = t[3 + i].w;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kMaxPts; ++k) {
+    const float l0 = VSP(10, k), l1 = VSP(11, k), l2 = VSP(12, k);
+    float n0 = fmaxf(0.f, fmaf(beta, dr[3 * k], l0));
+    float n1 = fmaf(beta, dr[3 * k + 1], l1), n2 = fmaf(beta, dr[3 * k + 2], l2);
+    const float lim = R.mu * n0;
+    if constexpr (kCone) {
+      const float m2 = n1 * n1 + n2 * n2;
+      const float sc = m2 > lim * lim ? lim * rsqrtf(m2) : 1.f;
+      n1 *= sc;
+      n2 *= sc;
+    } else {
+      n1 = fminf(fmaxf(n1, -lim), lim);
+      n2 = fminf(fmaxf(n2, -lim), lim);
+    }
+    dr[3 * k] = (l0 - ls[3 * k]) + beta * dr[3 * k];
+    dr[3 * k + 1] = (l1 - ls[3 * k + 1]) + beta * dr[3 * k + 1];
+    dr[3 * k + 2] = (l2 - ls[3 * k + 2]) + beta * dr[3 * k + 2];
+    ls[3 * k] = n0; ls[3 * k + 1] = n1; ls[3 * k + 2] = n2;
+    VSP(10, k) = n0; VSP(11, k) = n1; VSP(12, k) = n2;
+    const float d0 = n0 - l0, d1 = n1 - l1, d2 = n2 - l2;
+    const float3 p = f3(VSP(0, k), VSP(1, k), VSP(2, k));
+    apply_point(R, p - R.xa, p - R.xb, d0 * R.n + d1 * R.t1 + d2 * R.t2);
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    a4[i] = make_float4(ls[4 * i], ls[4 * i + 1], ls[4 * i + 2], ls[4 * i + 3]);
+    a4[3 + i] = make_float4(dr[4 * i], dr[4 * i + 1], dr[4 * i + 2], dr[4 * i + 3]);
+  }
+  if (R.da) { vst3(V, FV, R.a, R.va); vst3(V, FW, R.a, R.wa); }
+  if (R.db) { vst3(V, FV, R.b, R.vb); vst3(V, FW, R.b, R.wb); }
+}
+
+// The step over every colour in order (pairs of one colour share no dynamic
+// body; the serial colour runs on one lane).
+template <bool kS, bool kCone>
+__device__ __noinline__ void accel_step_t(const SolverRef r, float* __restrict__ acc, const int* __restrict__ off,
+                                          int ncol, int lane, float beta) {
+  const SolverView<kS> V(r);
+  for (int c = 0; c < ncol; ++c) {
+    const int s0 = off[c], s1 = off[c + 1];
+    if (c == kSerial) {
+      if (lane == 0)
+        for (int sl = s0; sl < s1; ++sl) accel_pair<kS, kCone>(V, acc, sl, beta);
+    } else {
+      for (int sl = s0 + lane; sl < s1; sl += 32) accel_pair<kS, kCone>(V, acc, sl, beta);
+    }
+    __syncwarp();
+  }
+}
+
+__device__ __forceinline__ void accel_begin(const SolverRef& r, float* acc, int npairs, int lane) {
+  if (r.shared) accel_begin_t<true>(r, acc, npairs, lane);
+  else accel_begin_t<false>(r, acc, npairs, lane);
+  __syncwarp();
+}
+__device__ __forceinline__ float accel_change2(const SolverRef& r, const float* acc, int npairs, int lane) {
+  return r.shared ? accel_change2_t<true>(r, acc, npairs, lane) : accel_change2_t<false>(r, acc, npairs, lane);
+}
+__device__ __forceinline__ void accel_step(const SolverRef& r, float* acc, const int* off, int ncol, int lane, float beta,
+                                           bool cone) {
+  if (cone) {
+    if (r.shared) accel_step_t<true, true>(r, acc, off, ncol, lane, beta);
+    else accel_step_t<false, true>(r, acc, off, ncol, lane, beta);
+  } else {
+    if (r.shared) accel_step_t<true, false>(r, acc, off, ncol, lane, beta);
+    else accel_step_t<false, false>(r, acc, off, ncol, lane, beta);
+  }
+}
+#undef VSP
+#undef VSF
 
 #undef VF
 
@@ -1083,9 +1217,9 @@ __device__ StepOut substep(const Dev& D, const Ep& E, EpState& st, float h) {
   __syncwarp();
 
   // (5) colouring, redone every step: greedy (lowest colour free at both
-  // dynamic bodies) over the pairs in order of key = (contact height in 1 mm
-  // bins ascending, natural index descending).  The colours are swept in
-  // index order, so lower contacts tend to be solved first; on 18-level
+  // dynamic bodies) over the pairs in order of key = (lower body a
+  // ascending, upper body b descending).  The colours are swept in index
+  // order, so contacts low in the tower tend to be solved first; on 18-level
   // towers this order needs several times fewer sweeps to reach a residual
   // tolerance than colouring in natural order, at the same colour count.
   // The candidate array (free after the narrowphase) holds the order.
@@ -1094,24 +1228,17 @@ __device__ StepOut substep(const Dev& D, const Ep& E, EpState& st, float h) {
     const int nchunk = (npairs + 31) / 32;
     for (int p0 = 0; p0 < npairs; p0 += 32) {
       int p = p0 + lane;
-      uint32_t key = 0xffffffffu;
-      if (p < npairs) {
-        float z = Bc.pt[(size_t)p * kMaxPts * kNatPtFloats + 2];
-        int bin = (int)floorf((z + 5e-4f) * 1000.f);
-        bin = min(max(bin + 1, 0), 65535);
-        key = ((uint32_t)bin << 16) | (uint32_t)(0xffff - p);
-      }
+      // key ((a + 1) << 16) | b of the pair -> ((a + 1) << 16) | (0xffff - b)
+      auto colour_key = [&](int q) {
+        const uint32_t k = Bc.key[q];
+        return (k & 0xffff0000u) | (0xffffu - (k & 0xffffu));
+      };
+      uint32_t key = p < npairs ? colour_key(p) : 0xffffffffu;
       // rank among all pairs: keys are distinct
       int rank = 0;
       for (int c = 0; c < nchunk; ++c) {
         int q = c * 32 + lane;
-        uint32_t kq = 0xffffffffu;
-        if (q < npairs) {
-          float zq = Bc.pt[(size_t)q * kMaxPts * kNatPtFloats + 2];
-          int bq = (int)floorf((zq + 5e-4f) * 1000.f);
-          bq = min(max(bq + 1, 0), 65535);
-          kq = ((uint32_t)bq << 16) | (uint32_t)(0xffff - q);
-        }
+        uint32_t kq = q < npairs ? colour_key(q) : 0xffffffffu;
         for (int j = 0; j < 32; ++j) rank += __shfl_sync(FULL, kq, j) < key;
       }
       if (p < npairs) ord[rank] = (uint32_t)p;
@@ -1304,10 +1431,21 @@ __device__ StepOut substep(const Dev& D, const Ep& E, EpState& st, float h) {
     float win_res = -1.f;   // residual at the start of the current stall window
     int win_at = 0;
     bool stalled = false;
+    const int am = Pm.accel_period;
+    float* acc = D.acc + E.poff * kAccFloats;
+    float r2_prev = 0.f;
+    if (am > 0) accel_begin(V, acc, npairs, lane);
     while (sweeps < cap) {
       colour_passes<1>(V, s.off, ncol, lane, e1om, om, Pm.sweep_order == 1 && (sweeps & 1), Pm.beta, Pm.slop,
                        Pm.friction_cone != 0);
       ++sweeps;
+      if (am > 0 && sweeps % am == 0) {
+        const float r2 = accel_change2(V, acc, npairs, lane);
+        float beta = r2_prev > 0.f ? r2 / r2_prev : 0.f;
+        if (!(beta <= 1.f)) beta = 0.f;   // restart (and NaN)
+        r2_prev = r2;
+        accel_step(V, acc, s.off, ncol, lane, beta, Pm.friction_cone != 0);
+      }
       if (sweeps >= next || sweeps == cap) {
         res = episode_residual(V, npairs, lane, Pm.friction_cone != 0);
         if (!rmode || res <= Pm.residual_tol || !(res == res)) break;

@@ -486,14 +486,16 @@ def test_episode_statistics_on_hand_set_states(cuda_device):
         assert abs(sg["com_imbalance"][e] - w.com_imbalance(e)) < 1e-6
 
 
-def test_full_friction_batch_sampled_against_the_oracle(cuda_device):
+@pytest.mark.parametrize("accel", [0, 64])
+def test_full_friction_batch_sampled_against_the_oracle(cuda_device, accel):
     """The 450-episode batch in the benchmark's launch configuration (one
-    persistent launch, every episode resident): one converged step from the
-    initial state on the GPU, and six sampled episodes recomputed by the
-    oracle, within the one-step parity bounds."""
+    persistent launch, every episode resident; plain and accelerated
+    sweeps): one converged step from the initial state on the GPU, and six
+    sampled episodes recomputed by the oracle's plain PGS, within the
+    one-step parity bounds."""
     scene, prot, prm = synth.friction_workload(seed=1)
     prm = dict(prm, residual_tol=1e-6, pgs_iter_cap=200000)
-    b = jb().Batch(scene, prm)
+    b = jb().Batch(scene, dict(prm, pgs_accel_period=accel))
     b.step(1)
     st = b.stats()
     assert (st["status"] == 0).all() and (st["last_residual"] <= 1e-6).all()
@@ -534,18 +536,21 @@ def test_newton_restitution_fp32_and_parity(cuda_device):
     assert ev < 1e-4 and ew < 1e-4, (ev, ew)
 
 
+@pytest.mark.parametrize("accel", [0, 4])
 @pytest.mark.parametrize("name", ["tower18", "tower4_perturbed"])
-def test_fixed_sweeps_match_the_oracle_in_colour_order(cuda_device, name):
+def test_fixed_sweeps_match_the_oracle_in_colour_order(cuda_device, name, accel):
     """With the oracle sweeping in the library's colour order, the iterates
     themselves agree, not only the fixed point: one step of 20 fixed sweeps
     (far from converged) gives the same state up to FP32 rounding.  This
     checks the sweep arithmetic (the point-block rows, the packed impulse
-    application, the colour schedule) row for row."""
+    application, the colour schedule) row for row, and with accel = 4 the
+    five conjugate-gradient steps in between (direction, beta, restart,
+    projection, impulse application)."""
     if name == "tower18":
         scene = synth.build_scene([synth.Tower()], 0)
     else:
         scene = synth.perturbed(synth.build_scene([synth.Tower(levels=4, mu=0.5)], 1), 5, dx=2e-4, dang=0.01)
-    prm = synth.params(pgs_iters=20)
+    prm = synth.params(pgs_iters=20, pgs_accel_period=accel)
     b = jb().Batch(scene, prm)
     w = oracle.World(as64(scene), dict(prm, colour_order=1))
     b.step(1)
@@ -559,3 +564,41 @@ def test_fixed_sweeps_match_the_oracle_in_colour_order(cuda_device, name):
     wn = oracle.World(as64(scene), prm)
     wn.step(1)
     assert np.abs(wn.state()[2] - vo).max() > 1e-5
+    if accel:
+        # and so is the plain solve's in the same order: the agreement is the acceleration's
+        wp = oracle.World(as64(scene), dict(prm, colour_order=1, pgs_accel_period=0))
+        wp.step(1)
+        assert np.abs(wp.state()[2] - vo).max() > 1e-5
+
+
+@pytest.mark.parametrize("period", [8, 64])
+@pytest.mark.parametrize("name", ["tower4_perturbed", "tower18", "pile"])
+def test_accelerated_solve_converges_to_the_oracle(cuda_device, name, period):
+    """The conjugate-gradient acceleration changes the iterates and the sweep
+    count, not the fixed point: converged to 1e-6 the GPU's accelerated step
+    matches the oracle's plain sequential PGS within the one-step bounds
+    (the pile: positions and the residual, as for the relaxed sweeps), in
+    fewer sweeps than the GPU's own plain solve."""
+    if name == "tower4_perturbed":
+        scene = synth.perturbed(synth.build_scene([synth.Tower(levels=4, mu=0.5)], 1), 5, dx=2e-4, dang=0.01)
+    elif name == "pile":
+        scene = synth.pile_scene(28, seed=5)
+    else:
+        scene = synth.build_scene([synth.Tower()], 0)
+    prm = synth.params(residual_tol=1e-6, pgs_iter_cap=200000)
+    b = jb().Batch(scene, dict(prm, pgs_accel_period=period))
+    p = jb().Batch(scene, prm)
+    w = oracle.World(as64(scene), prm)
+    b.step(1)
+    p.step(1)
+    w.step(1)
+    st = b.stats()
+    assert st["status"][0] == 0 and st["last_residual"][0] <= 1e-6
+    if name == "tower18":
+        assert st["last_sweeps"][0] < p.stats()["last_sweeps"][0], (st["last_sweeps"][0], p.stats()["last_sweeps"][0])
+    xg, qg, vg, wg = b.state()
+    xo, qo, vo, wo = w.state()
+    assert np.abs(xg - xo).max() < 1e-5
+    if name != "pile":
+        ev, ew = velocity_error(scene, vg, wg, vo, wo)
+        assert ev < 1e-4 and ew < 1e-4, (ev, ew)

@@ -761,6 +761,65 @@ def test_colour_order_keeps_the_fixed_point():
     assert np.abs(out["fixed", 0][2] - out["fixed", 1][2]).max() > 1e-5
 
 
+def _flush_stack(n, hz=0.0075):
+    """n blocks stacked flush on the ground in FP64 (no jitter)."""
+    half = np.tile(np.array([[0.0375], [0.0125], [hz]]), (1, n))
+    x = np.zeros((3, n))
+    x[2] = hz + 2 * hz * np.arange(n)
+    q = np.zeros((4, n))
+    q[0] = 1
+    return synth.Scene(np.array([0, n], np.int32), half, np.full(n, 0.015), np.full(n, 0.4), x, q,
+                       np.zeros((3, n)), np.zeros((3, n)), np.array([0.4]))
+
+
+@pytest.mark.parametrize("period", [1, 4, 16])
+def test_acceleration_reaches_the_stack_lcp(period):
+    """The accelerated solve (a nonsmooth conjugate-gradient step every m
+    sweeps) lands on the LCP solution of a resting stack: after one step from
+    rest every block is at rest again, and the interface below block i carries
+    the weight of the n - i blocks above it times h, exactly (the per-point
+    split is not unique, the total is).  It needs a fraction of plain PGS's
+    sweeps to get there.  A wrong sign or factor in the direction update
+    slows or stalls it; a step not applied to the bodies, or left
+    unprojected, leaves velocities or totals off."""
+    n = 6
+    sc = _flush_stack(n)
+    mgh = 0.015 * 9.81 / 240.0
+    sweeps = {}
+    for m in (0, period):
+        W = oracle.World(sc, synth.params(residual_tol=1e-10, pgs_iter_cap=2000000, pgs_accel_period=m))
+        W.step(1)
+        st = W.stats()
+        assert st["status"][0] == 0 and st["last_residual"][0] <= 1e-10
+        sweeps[m] = int(st["last_sweeps"][0])
+        x, q, v, w = W.state()
+        assert np.abs(v).max() < 1e-8 and np.abs(w).max() < 1e-6
+        tot = {(r["a"], r["b"]): sum(l[0] for l in r["lam"][:r["np"]]) for r in oracle.contact_dicts(W.contacts(0))}
+        assert sorted(tot) == [(-1, 0)] + [(i, i + 1) for i in range(n - 1)]
+        for (a, b), lam in tot.items():
+            assert abs(lam / mgh - (n - b)) < 1e-7, ((a, b), lam / mgh)
+    assert sweeps[period] < sweeps[0] / 2, sweeps
+
+
+def test_acceleration_keeps_the_fixed_point():
+    """With friction active (a perturbed tower) the accelerated and the plain
+    solve, converged tightly, give the same velocities; after a fixed 40
+    sweeps they differ (the option takes effect)."""
+    sc = synth.perturbed(synth.build_scene([synth.Tower(levels=4, mu=0.5)], 1), 5, dx=2e-4, dang=0.01)
+    s64 = synth.Scene(sc.body_off, *[getattr(sc, k).astype(np.float64) for k in
+                                     ("half", "mass", "mu", "x", "q", "v", "w", "ground_mu")])
+    out = {}
+    for name, prm in (("conv", dict(residual_tol=1e-11, pgs_iter_cap=2000000)), ("fixed", dict(pgs_iters=40))):
+        for m in (0, 8):
+            W = oracle.World(s64, synth.params(pgs_accel_period=m, **prm))
+            W.step(1)
+            assert W.stats()["status"][0] == 0
+            out[name, m] = W.state()
+    assert np.abs(out["conv", 0][2] - out["conv", 8][2]).max() < 1e-7
+    assert np.abs(out["conv", 0][3] - out["conv", 8][3]).max() < 1e-5
+    assert np.abs(out["fixed", 0][2] - out["fixed", 8][2]).max() > 1e-6
+
+
 # --------------------------------------------- Sec. 6.2.1 reduction to 4 points
 def _hull_area_xy(P):
     """Largest polygon area over the orderings of a few xy points (brute
