@@ -43,7 +43,6 @@ FLOP_POINT_SETUP = 180.0
 FLOP_PAIR = 750.0
 FLOP_BP = 12.0
 FLOP_BODY = 60.0
-SMS, FP32_LANES = 152, 128
 
 
 def parse():
@@ -63,6 +62,8 @@ def parse():
     ap.add_argument("--fixed-iters", type=int, default=0,
                     help="fixed-sweep mode with this many sweeps per solve (profiling)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the learned-vs-plain comparison over seeds and the unaccelerated plain arm")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="friction", choices=["friction", "ragged", "stress"],
                     help="friction: 450 x 18-level towers (the headline); ragged: 4096 towers of 6-30 levels; "
@@ -80,17 +81,23 @@ def parse():
     ap.add_argument("--train-rows", type=int, default=5_000_000)
     ap.add_argument("--gate-episodes", type=int, default=48)
     ap.add_argument("--gate-steps", type=int, default=480)
+    ap.add_argument("--k-rule", default="axis", choices=["axis", "ziglar"],
+                    help="push threshold multiplier: axis (Y 3, X 4; the workload's schedule) or ziglar "
+                         "(Tab. ziglar's move classes: side X 4, centre X and Y 3)")
+    ap.add_argument("--claims", action="store_true",
+                    help="evaluate Sec. 13.2's three claims over three seeds and both k rules (plain PGS), "
+                         "print one JSON line and exit")
     ap.add_argument("--cpu-episodes", type=int, default=0)
     ap.add_argument("--cpu-steps", type=int, default=30)
     return ap.parse_args()
 
 
-def make_workload(kind, seed):
+def make_workload(kind, seed, k_rule="axis"):
     if kind == "ragged":
         return synth.ragged_workload(seed=seed)
     if kind == "stress":
         return synth.stress_workload(seed=seed)
-    return synth.friction_workload(seed=seed)
+    return synth.friction_workload(seed=seed, k_rule=k_rule)
 
 
 WORKLOAD_SEED = {"friction": 1, "ragged": 2, "stress": 5}
@@ -100,9 +107,10 @@ WORKLOAD_NAME = {"friction": "450 episodes x 18-level towers, mu {0.25,0.40,0.60
                            "on a level in 10..30, 720 steps"}
 
 
-def workload(args, rank):
+def workload(args, rank, seed=None):
     kind = getattr(args, "workload", "friction")
-    scene, prot, prm = make_workload(kind, WORKLOAD_SEED[kind] + rank)
+    scene, prot, prm = make_workload(kind, (WORKLOAD_SEED[kind] if seed is None else seed) + rank,
+                                     getattr(args, "k_rule", "axis"))
     if kind == "stress" and not args.episodes:
         args.episodes = 152     # one 48-level episode per SM of the 16384
     if args.episodes:
@@ -241,6 +249,17 @@ def outcomes(scene, prot, st):
             kd[0] += 1
             kd[1] += int(bool(st["collapsed"][e]) and j == n_att - 1)
     out["by_move"] = {k: {"moves": v[0], "collapses": v[1], "rate": v[1] / max(v[0], 1)} for k, v in sorted(kinds.items())}
+    # Eq. stability as an early warning: the device's per-step margin went
+    # negative before (or at) the step where Eq. collapse fired
+    if "first_unstable_step" in st:
+        col = np.asarray(st["collapsed"]) > 0
+        fu, cs = np.asarray(st["first_unstable_step"]), np.asarray(st["collapse_step"])
+        warned = col & (fu >= 1) & (fu <= cs)
+        lead = (cs - fu)[warned]
+        out["early_warning"] = {"collapsed": int(col.sum()), "warned_before_collapse": int(warned.sum()),
+                                "median_lead_steps": float(np.median(lead)) if len(lead) else None,
+                                "standing_with_negative_margin": int(((~col) & (fu >= 1)).sum()),
+                                "standing": int((~col).sum())}
     return out
 
 
@@ -311,7 +330,7 @@ def cpu_baseline(args, scene, prot, prm):
     s, p = synth.subset(scene, prot, idx)
     s64 = synth.Scene(s.body_off, *[getattr(s, k).astype(np.float64) for k in
                                     ("half", "mass", "mu", "x", "q", "v", "w", "ground_mu")])
-    w = oracle.World(s64, prm)
+    w = oracle.World(s64, dict(prm, pgs_accel_period=0, colour_order=0))
     w.set_protocol(p)
     t0 = time.perf_counter()
     w.run_protocol(max_steps=args.cpu_steps, threads=ncores)
@@ -320,8 +339,10 @@ def cpu_baseline(args, scene, prot, prm):
     bs = float(st["body_steps"].sum())
     return {"value": bs / dt, "unit": "body-steps/s", "cores": ncores, "kind": "oracle",
             "sample": f"first {args.cpu_steps} steps of {ne} of the {scene.n_episodes} episodes "
-                      f"(evenly spaced over the three mu levels), FP64, OpenMP over episodes",
-            "seconds": dt, "sweeps_per_solve": float(st["total_sweeps"].sum() / max(st["solves"].sum(), 1))}
+                      f"(evenly spaced over the three mu levels), FP64, plain PGS in natural order, "
+                      f"OpenMP over episodes",
+            "seconds": dt, "episodes": ne,
+            "sweeps_per_solve": float(st["total_sweeps"].sum() / max(st["solves"].sum(), 1))}
 
 
 def run_reference(args):
@@ -348,10 +369,80 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def claims(args):
+    """Sec. 13.2's three claims on the friction workload, per seed and per
+    threshold rule: (1) side_yaxis moves collapse less often than side_xaxis
+    moves; (2) the centre block pushed along X (center_xaxis) is the safest
+    move; (3) the collapse rate falls as mu_s rises.  A collapse is charged to
+    the move in progress.  Forces are F = k mu_s m g, so the pushes scale with
+    the friction they meet: nothing in the schedule makes higher mu_s safer,
+    and claim (3) can only come from the dynamics."""
+    import torch
+    import paper_2606_28394_gb300 as jb
+    dev = torch.device("cuda", 0)
+    out = {"claims": "Sec. 13.2: side_y < side_x; centre_x safest; collapse rate falls with mu_s", "runs": []}
+    for rule in ("axis", "ziglar"):
+        for sd in COMPARE_SEEDS:
+            a2 = argparse.Namespace(**vars(args))
+            a2.k_rule = rule
+            sc, pr, prm = workload(a2, 0, seed=sd)
+            b = jb.Batch(sc, dict(prm, warm_start=1), max_moves=int(pr.off[-1]), device=dev)
+            b.set_protocol(pr)
+            b.run_protocol(1 << 30)
+            st = b.stats()
+            o = outcomes(sc, pr, st)
+            by = o["by_move"]
+            rates = {k: v["rate"] for k, v in by.items()}
+            per_mu = [o[m]["collapsed"] / o[m]["episodes"] for m in ("0.25", "0.40", "0.60")]
+            out["runs"].append({"k_rule": rule, "seed": sd, "by_move": by, "collapse_rate_per_mu": per_mu,
+                                "claim1_side_y_below_side_x": rates.get("side_y", 0) < rates.get("side_x", 0),
+                                "claim2_centre_x_safest": rates.get("centre_x", 1) <= min(rates.values()),
+                                "claim3_falls_with_mu": per_mu[0] > per_mu[1] > per_mu[2]})
+    for rule in ("axis", "ziglar"):
+        runs = [r for r in out["runs"] if r["k_rule"] == rule]
+        out[rule] = {c: sum(r[c] for r in runs) for c in ("claim1_side_y_below_side_x", "claim2_centre_x_safest",
+                                                           "claim3_falls_with_mu")} | {"seeds": len(runs)}
+    print(json.dumps(out))
+
+
+def fp32_peak(jb, torch, dev, stream):
+    """The FP32 multiply-add rate of this GPU, measured with the library's own
+    probe kernel (8 independent FMA chains per thread, 8 CTAs of 256 threads
+    per SM, scalar FFMA and packed FFMA2), CUDA events on the launching
+    stream, best of 5 launches each after a warm-up launch."""
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, iters = 8 * nsm, 1 << 13
+    sink = torch.empty(blocks * 256, dtype=torch.float32, device=dev)
+    out = {"sms": nsm, "blocks": blocks, "threads": 256, "iters": iters}
+    for packed, name in ((0, "ffma"), (1, "ffma2")):
+        flops = jb.jb_fma_probe_flops(packed, blocks, iters)
+        best = float("inf")
+        for rep in range(6):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            jb.check(jb.jb_fma_probe(packed, blocks, iters, sink.data_ptr(), C_stream(stream)), "jb_fma_probe")
+            e1.record(stream)
+            e1.synchronize()
+            if rep:
+                best = min(best, e0.elapsed_time(e1))
+        out[name + "_tflops"] = flops / (best / 1e3) / 1e12
+    out["peak_tflops"] = max(out["ffma_tflops"], out["ffma2_tflops"])
+    return out
+
+
+def C_stream(stream):
+    return stream.cuda_stream
+
+
+COMPARE_SEEDS = (1, 1001, 2001)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.claims:
+        return claims(args)
     import torch
     import torch.distributed as dist
     import paper_2606_28394_gb300 as jb
@@ -376,11 +467,16 @@ def main():
     stream = torch.cuda.current_stream(dev)
     ws = jb.Batch(scene, prm, max_moves=M, stream=stream, device=dev).workspace   # allocated once
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
-    h2d = (scene.body_off.nbytes + scene.half.nbytes + scene.mass.nbytes + scene.mu.nbytes
-           + scene.x.nbytes + scene.q.nbytes + scene.v.nbytes + scene.w.nbytes + scene.ground_mu.nbytes
-           + sum(getattr(prot, f).nbytes for f in ("off", "block", "axis", "sign", "factor", "k",
-                                                    "remove", "push_steps", "settle_steps")))
-    d2h = scene.n_episodes * jb.C.sizeof(jb.jb_episode_stats)
+
+    def io_bytes(sc, pr):
+        h2d = (sc.body_off.nbytes + sc.half.nbytes + sc.mass.nbytes + sc.mu.nbytes
+               + sc.x.nbytes + sc.q.nbytes + sc.v.nbytes + sc.w.nbytes + sc.ground_mu.nbytes
+               + sum(getattr(pr, f).nbytes for f in ("off", "block", "axis", "sign", "factor", "k",
+                                                      "remove", "push_steps", "settle_steps")))
+        return h2d, sc.n_episodes * jb.C.sizeof(jb.jb_episode_stats)
+
+    h2d, d2h = io_bytes(scene, prot)
+    peak = fp32_peak(jb, torch, dev, stream)
 
     tuning = None
     if args.autotune:
@@ -390,27 +486,33 @@ def main():
     net, learned = None, None
     if args.warm_start == "learned":
         net, learned = prepare_learned(args, rank, prm, dev)
-    run_prm = dict(prm, warm_start=2 if (learned and learned["kept"]) else 1)
+    plain_prm = dict(prm, warm_start=1)
+    learned_prm = dict(prm, warm_start=2) if net is not None else None
+    kept = bool(learned and learned["kept"])
+    run_prm = learned_prm if kept else plain_prm
 
     launches = [1]
 
-    def job(max_steps, params=None):
+    def job(max_steps, params=None, sc=None, pr=None, work=None):
         """One pass through the C ABI from host buffers: create the batch
         (scene upload), upload the schedule, run every episode through it in
         one persistent launch, read the statistics back.  CUDA events bracket
         the launch (inputs resident); the host clock brackets the whole pass."""
         params = params or run_prm
+        sc = sc if sc is not None else scene
+        pr = pr if pr is not None else prot
         flush.fill_(1)
         torch.cuda.synchronize(dev)
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         t0 = time.perf_counter()
-        b = jb.Batch(scene, params, max_moves=M, stream=stream, device=dev, workspace=ws)
+        b = jb.Batch(sc, params, max_moves=int(pr.off[-1]), stream=stream, device=dev,
+                     workspace=work if work is not None else ws)
         launches[0] = len(b.size_classes())     # episode-kernel launches per run_protocol
         if params["warm_start"] >= 2:
             jb.check(jb.jb_set_warmstart_mlp(b.h, net.block.data_ptr()), "jb_set_warmstart_mlp")
-        b.set_protocol(prot)
+        b.set_protocol(pr)
         e0.record(stream)
         b.run_protocol(max_steps)
         e1.record(stream)
@@ -419,6 +521,12 @@ def main():
         t1 = time.perf_counter()
         barrier()
         return e0.elapsed_time(e1), t1 - t0, st
+
+    def rate(ms, st):
+        return float(st["body_steps"].sum()) / (ms / 1e3)
+
+    def sps(st):
+        return float(st["total_sweeps"].sum() / max(st["solves"].sum(), 1))
 
     # warm-up: the same launch path on the job truncated to a few physics steps
     for _ in range(args.warmup):
@@ -433,16 +541,48 @@ def main():
     body_steps = float(st["body_steps"].sum())
     flops = algorithmic_flops(st)
     mlp_flops = MLP_FLOP * float(st["mlp_points"].sum())
-    plain = None
-    if run_prm["warm_start"] >= 2:
-        # the comparison arm: the same job with plain PGS (previous-frame warm start)
-        ms_p, _, st_p = job(args.max_steps, dict(prm, warm_start=1))
-        ms_pm, _, bs_p = reduce_ranks(ms_p, 0.0, float(st_p["body_steps"].sum()), dev, dist if world > 1 else None)
-        plain = {"value": bs_p / (ms_pm / 1e3), "ms_per_step": ms_pm,
-                 "sweeps_per_solve": float(st_p["total_sweeps"].sum() / max(st_p["solves"].sum(), 1))}
     ms_max, wall_max, total_body_steps = reduce_ranks(ms, sum(walls), body_steps * args.steps, dev,
                                                        dist if world > 1 else None)
     value = total_body_steps / (ms_max / 1e3)
+
+    # learned warm start against plain PGS: both arms on the same job, for
+    # the benchmark's seed and two more seeds of the same workload (whole
+    # episodes are chaotic, so one seed's ratio carries trajectory noise)
+    compare = None
+    if net is not None and not args.no_compare:
+        per_seed = []
+        for sd in COMPARE_SEEDS:
+            if sd == WORKLOAD_SEED[args.workload]:
+                sc_s, pr_s = scene, prot
+            else:
+                a2 = argparse.Namespace(**vars(args))
+                sc_s, pr_s, _ = workload(a2, rank, seed=sd)
+                sc_s, pr_s = pinned_inputs(sc_s, pr_s, torch)
+            arms = {}
+            for name, p_ in (("plain", plain_prm), ("learned", learned_prm)):
+                if sc_s is scene and p_ is run_prm:
+                    arms[name] = (ms / args.steps, st)   # the timed runs above
+                else:
+                    ms_a, _, st_a = job(args.max_steps, p_, sc_s, pr_s)
+                    arms[name] = (ms_a, st_a)
+            per_seed.append({"seed": sd, "plain_body_steps_per_s": rate(*arms["plain"]),
+                             "learned_body_steps_per_s": rate(*arms["learned"]),
+                             "plain_sweeps_per_solve": sps(arms["plain"][1]),
+                             "learned_sweeps_per_solve": sps(arms["learned"][1]),
+                             "learned_points": float(arms["learned"][1]["mlp_points"].sum()),
+                             "point_solves": float(arms["learned"][1]["point_steps"].sum()),
+                             "learned_over_plain": rate(*arms["learned"]) / rate(*arms["plain"])})
+        ratios = [r["learned_over_plain"] for r in per_seed]
+        compare = {"seeds": per_seed, "learned_over_plain_mean": statistics.mean(ratios),
+                   "learned_over_plain_min": min(ratios), "learned_over_plain_max": max(ratios),
+                   "note": "each seed: the whole 450-episode job once per arm; the spread across seeds is "
+                           "trajectory noise (chaotic collapses), the work inside one seed is deterministic"}
+    # the paper's plain PGS without the conjugate-gradient steps, same job (context)
+    unaccel = None
+    if prm.get("pgs_accel_period", 0) and not args.no_compare:
+        ms_u, _, st_u = job(args.max_steps, dict(plain_prm, pgs_accel_period=0))
+        unaccel = {"value": rate(ms_u, st_u), "ms_per_step": ms_u, "sweeps_per_solve": sps(st_u),
+                   "capped_fraction": float(st_u["capped_solves"].sum() / max(st_u["solves"].sum(), 1))}
     e2e = None
     if not args.no_e2e:
         e2e = {"value": total_body_steps / wall_max, "unit": "body-steps/s",
@@ -452,8 +592,7 @@ def main():
                        "jb_set_protocol, jb_run_protocol, jb_read_episode_stats"}
 
     peaks = load_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_tf = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    peak_tf = peak["peak_tflops"]
     achieved = flops / (ms / args.steps / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
             "frac": achieved / peak_tf,
@@ -462,9 +601,13 @@ def main():
                                              and not args.fixed_iters) else None),
             "mlp_flops_per_launch": mlp_flops,
             "mlp_roofline_ms": mlp_flops / (float(peaks.get("bf16_tflops", 1892.9)) * 1e12) * 1e3,
-            "peak_note": f"FP32 FMA peak: {SMS} SMs x {FP32_LANES} lanes x 2 flop x {sm_max:.0f} MHz (max SM clock of measured)",
+            "peak_note": (f"measured FP32 multiply-add rate of this GPU (jb_fma_probe, {peak['sms']} SMs from the "
+                          f"device, {peak['blocks']} CTAs x 256 threads x 8 chains, best of 5): FFMA "
+                          f"{peak['ffma_tflops']:.1f}, FFMA2 {peak['ffma2_tflops']:.1f} TFLOP/s; peak = the larger"),
             "kernel": "episode_kernel (persistent, one warp per episode)",
-            "flops_per_launch": flops}
+            "flops_per_launch": flops,
+            "work_basis": "algorithmic flops per unit x the GPU's own sweeps (colour order, conjugate-gradient "
+                          "steps every pgs_accel_period sweeps, residual checks at an adaptive cadence)"}
     line = {"metric": "body-steps/s at PGS residual <= 1e-5: learned warm start vs plain PGS",
             "value": value, "unit": "body-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -473,6 +616,7 @@ def main():
                                     f"{args.episodes} episodes (evenly spaced) of: {WORKLOAD_NAME[args.workload]}")
                                    + (f", fixed {args.fixed_iters} sweeps (profiling)" if args.fixed_iters else ""),
                        "residual_tol": args.tol, "pgs_iter_cap": args.cap, "max_steps": args.max_steps,
+                       "pgs_accel_period": prm.get("pgs_accel_period", 0),
                        "stall_window": jb.params_from_dict(run_prm).stall_window,
                        "residual_check_every": [jb.params_from_dict(run_prm).residual_every,
                                                 jb.params_from_dict(run_prm).residual_every_max],
@@ -480,17 +624,21 @@ def main():
                        "warmup": f"{args.warmup} passes of the job truncated to {args.warmup_steps} physics steps",
                        "episodes": scene.n_episodes, "bodies": scene.n_bodies},
             "warm_start": {"mode": "learned (network on unmatched points, previous-frame elsewhere)"
-                           if run_prm["warm_start"] >= 2 else "plain (previous-frame)",
-                           "training": learned, "plain_arm": plain,
-                           "learned_over_plain": (value / plain["value"]) if plain else None},
+                           if kept else "plain (previous-frame)"
+                           + (": the gate rejected the network" if learned else ""),
+                           "training": learned, "comparison": compare,
+                           "learned_over_plain": compare["learned_over_plain_mean"] if compare else None},
+            "plain_pgs_unaccelerated": unaccel,
             "autotune": tuning,
-            "roofline": roof, "gpu_launches": args.steps * launches[0], "clocks": clk.summary(),
+            "roofline": roof, "fp32_probe": peak, "gpu_launches": args.steps * launches[0],
+            "clocks": clk.summary(),
             "e2e": e2e,
-            "solver": {"sweeps_per_solve": float(st["total_sweeps"].sum() / max(st["solves"].sum(), 1)),
+            "solver": {"sweeps_per_solve": sps(st),
                        "not_converged_episodes": int(((st["status"] & jb.JB_EP_NOT_CONVERGED) != 0).sum()),
                        "solves": float(st["solves"].sum()),
                        "capped_solves": int(st["capped_solves"].sum()),
                        "capped_fraction": float(st["capped_solves"].sum() / max(st["solves"].sum(), 1)),
+                       "capped_in_collapsed_episodes": int(st["capped_solves"][st["collapsed"] > 0].sum()),
                        "sweeps_share_busiest_over_mean": float(st["total_sweeps"].max() / max(st["total_sweeps"].mean(), 1)),
                        "collapsed": int(st["collapsed"].sum()), "body_steps_per_job": body_steps,
                        "max_colours": int(st["max_colours"].max()),
@@ -499,7 +647,19 @@ def main():
                        "fixed_iters": args.fixed_iters}}
     line["outcomes"] = outcomes(scene, prot, st)
     if rank == 0 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(args, scene, prot, prm)
+        cb = cpu_baseline(args, scene, prot, prm)
+        # the GPU on the CPU leg's sample (same episodes, same steps): the same work side by side
+        idx = np.linspace(0, scene.n_episodes - 1, cb["episodes"]).round().astype(int)
+        s_c, p_c = synth.subset(scene, prot, idx)
+        b = jb.Batch(s_c, plain_prm, max_moves=int(p_c.off[-1]), stream=stream, device=dev)
+        b.set_protocol(p_c)
+        b.run_protocol(args.cpu_steps)
+        st_c = b.stats()
+        cb["gpu_sweeps_per_solve_same_sample"] = sps(st_c)
+        line["cpu_baseline"] = cb
+        # the work rate counted on the paper's plain PGS sweeps (the oracle's natural
+        # order on the same sample) rather than on the GPU's own
+        roof["frac_on_plain_pgs_sweeps"] = roof["frac"] * cb["sweeps_per_solve"] / max(sps(st_c), 1e-9)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -220,6 +220,15 @@ typedef struct {
      points, contact pairs, broadphase pair tests */
   double point_sweeps, point_steps, pair_steps, bp_tests;
   double mlp_points;        /* contact points whose start came from the warm-start network */
+  /* Eq. stability on the device after every step (same support polygon and
+     COM as com_imbalance): the margin after the last step (m, positive
+     inside), the smallest margin over the steps run, the first step (1-based
+     count) whose margin was negative and the step at which Eq. collapse
+     fired (-1 for none; both since creation or the last jb_set_protocol) */
+  float stability_margin;
+  float min_stability_margin;
+  int32_t first_unstable_step;
+  int32_t collapse_step;
 } jb_episode_stats;
 
 typedef struct jb_batch jb_batch;
@@ -431,6 +440,16 @@ jb_status jb_step_noalloc(int32_t n_episodes, const int32_t* body_off, const flo
                           const float* d_mass, const float* d_mu, const float* d_ground_mu,
                           float* d_x, float* d_q, float* d_v, float* d_w,
                           const jb_solver_params* p, int32_t n_steps, void* cuda_stream);
+
+/* Measurement utility (the paper has no counterpart): the FP32 multiply-add
+ * rate that bounds the step.  jb_fma_probe queues one launch of `blocks`
+ * CTAs of 256 threads, each thread running 8 independent multiply-add chains
+ * for `iters` rounds, scalar (packed = 0) or packed two-lane FFMA2
+ * (packed = 1), and writes one float per thread to d_sink (device, blocks *
+ * 256 floats).  jb_fma_probe_flops gives the launch's flop count (an FMA is 2
+ * flops), 0 for bad arguments.  The caller times the launch on cuda_stream. */
+jb_status jb_fma_probe(int32_t packed, int32_t blocks, int32_t iters, float* d_sink, void* cuda_stream);
+double jb_fma_probe_flops(int32_t packed, int32_t blocks, int32_t iters);
 
 const char* jb_status_str(jb_status s);
 const char* jb_last_error(void);

@@ -85,7 +85,9 @@ class jb_episode_stats(C.Structure):
                 ("total_sweeps", C.c_double), ("solves", C.c_double),
                 ("body_steps", C.c_double), ("point_sweeps", C.c_double),
                 ("point_steps", C.c_double), ("pair_steps", C.c_double),
-                ("bp_tests", C.c_double), ("mlp_points", C.c_double)]
+                ("bp_tests", C.c_double), ("mlp_points", C.c_double),
+                ("stability_margin", C.c_float), ("min_stability_margin", C.c_float),
+                ("first_unstable_step", C.c_int32), ("collapse_step", C.c_int32)]
 
 
 _vp = C.c_void_p
@@ -130,6 +132,8 @@ _sig = {
                                       C.c_float, C.c_float, C.c_float, _vp, _vp, C.c_size_t, _vp]),
     "jb_step_noalloc": (C.c_int32, [C.c_int32, _ip, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                     C.POINTER(jb_solver_params), C.c_int32, _vp]),
+    "jb_fma_probe": (C.c_int32, [C.c_int32, C.c_int32, C.c_int32, _vp, _vp]),
+    "jb_fma_probe_flops": (C.c_double, [C.c_int32, C.c_int32, C.c_int32]),
     "jb_status_str": (C.c_char_p, [C.c_int32]),
     "jb_last_error": (C.c_char_p, []),
     "jb_version": (C.c_char_p, []),

@@ -8,7 +8,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libjb.so")
-SOURCES = ["jb_kernels.cu", "jb_capi.cu", "jb_mlp.cu"]
+SOURCES = ["jb_kernels.cu", "jb_capi.cu", "jb_mlp.cu", "jb_peak.cu"]
 HEADERS = ["jb_internal.cuh", "jb_mlp.cuh", os.path.join("..", "..", "include", "jb.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -30,7 +30,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not _stale():
         return LIB
     tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "--threads", "3", "-shared",
+    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "--threads", "4", "-shared",
            "-Xcompiler", "-fPIC", "-o", tmp] + [os.path.join(CSRC, s) for s in SOURCES]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")

@@ -45,6 +45,8 @@ struct EpState {
   float last_res, max_res, kinetic, com_imb;
   double total_sweeps, solves, body_steps;
   double point_sweeps, point_steps, pair_steps, bp_tests, mlp_points;
+  float margin, min_margin;            // Eq. stability after the last step, smallest so far
+  int32_t first_unstable, collapse_step;   // 1-based step counts, -1 = none
 };
 
 struct Params {

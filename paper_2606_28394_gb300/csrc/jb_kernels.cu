@@ -1624,6 +1624,105 @@ __device__ void next_move(const Dev& D, const Ep& E, EpState& st) {
   else st.phase = JB_PH_DONE;
 }
 
+// Eq. stability on the warp's current state (frames must be current): the
+// signed distance from the COM (xy, mass-weighted over active dynamic blocks)
+// to the edges of the convex hull of the xy corners of the ground-touching
+// blocks (z - e_z <= aabb_eps), positive inside; minus the distance to the
+// hull's segment or point when it has fewer than 3 vertices; 0 when nothing
+// touches.  The corners go to the candidate array (free between substeps);
+// the hull is found by gift wrapping, each wrap step one warp reduction.
+__device__ __forceinline__ bool wrap_better(float2 cur, float2 a, float2 b) {
+  // b replaces a as the next hull vertex after cur
+  const float cr = (a.x - cur.x) * (b.y - cur.y) - (a.y - cur.y) * (b.x - cur.x);
+  const float da = (a.x - cur.x) * (a.x - cur.x) + (a.y - cur.y) * (a.y - cur.y);
+  const float db = (b.x - cur.x) * (b.x - cur.x) + (b.y - cur.y) * (b.y - cur.y);
+  return cr < 0.f || (cr == 0.f && db > da);
+}
+
+__device__ float support_margin_warp(const Dev& D, const Ep& E) {
+  const Sm& s = E.s;
+  const int lane = E.lane;
+  float2* P = reinterpret_cast<float2*>(s.cand);
+  float mx = 0.f, my = 0.f, mt = 0.f;
+  int cnt = 0;
+  for (int i0 = 0; i0 < E.nb; i0 += 32) {
+    const int i = i0 + lane;
+    bool touch = false;
+    if (i < E.nb) {
+      const int fl = s.flags[i];
+      if ((fl & kActive) && !(fl & kStatic)) {
+        const float m = D.mass[E.b0 + i];
+        mx += m * s.at(FX, i); my += m * s.at(FX + 1, i); mt += m;
+        touch = s.at(FX + 2, i) - s.at(FE + 2, i) <= D.P.aabb_eps;
+      }
+    }
+    const unsigned bal = __ballot_sync(FULL, touch);
+    if (touch) {
+      const int base = 8 * (cnt + __popc(bal & lanemask_lt(lane)));
+      const float3 a0 = s.axis(i, 0), a1 = s.axis(i, 1), a2 = s.axis(i, 2);
+      const float hx = s.at(FH, i), hy = s.at(FH + 1, i), hz = s.at(FH + 2, i);
+      for (int c = 0; c < 8; ++c) {
+        const float s0 = (c & 1) ? hx : -hx, s1 = (c & 2) ? hy : -hy, s2 = (c & 4) ? hz : -hz;
+        P[base + c] = make_float2(s.at(FX, i) + s0 * a0.x + s1 * a1.x + s2 * a2.x,
+                                  s.at(FX + 1, i) + s0 * a0.y + s1 * a1.y + s2 * a2.y);
+      }
+    }
+    cnt += __popc(bal);
+  }
+  mx = warp_sum(mx); my = warp_sum(my); mt = warp_sum(mt);
+  __syncwarp();
+  const int n = 8 * cnt;
+  if (!(mt > 0.f) || n == 0) return 0.f;
+  const float2 com = make_float2(mx / mt, my / mt);
+  // start: the lowest (x, then y) corner
+  float2 p0 = make_float2(FLT_MAX, FLT_MAX);
+  for (int j = lane; j < n; j += 32) {
+    const float2 p = P[j];
+    if (p.x < p0.x || (p.x == p0.x && p.y < p0.y)) p0 = p;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float2 q = make_float2(__shfl_xor_sync(FULL, p0.x, o), __shfl_xor_sync(FULL, p0.y, o));
+    if (q.x < p0.x || (q.x == p0.x && q.y < p0.y)) p0 = q;
+  }
+  float dmin = FLT_MAX;
+  float2 cur = p0, first = p0;
+  int nh = 0;
+  for (int it = 0; it < n + 2; ++it) {
+    float2 nx = cur;
+    bool have = false;
+    for (int j = lane; j < n; j += 32) {
+      const float2 p = P[j];
+      if (p.x == cur.x && p.y == cur.y) continue;
+      if (!have || wrap_better(cur, nx, p)) { nx = p; have = true; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float2 q = make_float2(__shfl_xor_sync(FULL, nx.x, o), __shfl_xor_sync(FULL, nx.y, o));
+      const bool qh = __shfl_xor_sync(FULL, (int)have, o) != 0;
+      if (qh && (!have || wrap_better(cur, nx, q))) { nx = q; have = true; }
+    }
+    // every lane now holds the same candidate up to ties of equal rank; take lane 0's
+    nx = make_float2(__shfl_sync(FULL, nx.x, 0), __shfl_sync(FULL, nx.y, 0));
+    have = __shfl_sync(FULL, (int)have, 0) != 0;
+    if (!have) break;
+    if (nh == 0) first = nx;
+    const float ex = nx.x - cur.x, ey = nx.y - cur.y;
+    const float len = sqrtf(ex * ex + ey * ey);
+    if (len > 0.f) dmin = fminf(dmin, (ex * (com.y - cur.y) - ey * (com.x - cur.x)) / len);
+    ++nh;
+    cur = nx;
+    if (cur.x == p0.x && cur.y == p0.y) break;
+  }
+  if (nh >= 3) return dmin;
+  if (nh == 0) return -sqrtf((com.x - p0.x) * (com.x - p0.x) + (com.y - p0.y) * (com.y - p0.y));
+  const float ex = first.x - p0.x, ey = first.y - p0.y;
+  const float l2 = ex * ex + ey * ey;
+  const float t = l2 > 0.f ? fminf(fmaxf(((com.x - p0.x) * ex + (com.y - p0.y) * ey) / l2, 0.f), 1.f) : 0.f;
+  const float dx = com.x - (p0.x + t * ex), dy = com.y - (p0.y + t * ey);
+  return -sqrtf(dx * dx + dy * dy);
+}
+
 __device__ void run_episode(const Dev& D, int e, int mode, int max_steps, unsigned char* base, int lane) {
   Ep E;
   E.e = e;
@@ -1709,14 +1808,19 @@ __device__ void run_episode(const Dev& D, int e, int mode, int max_steps, unsign
       if (st.phase != JB_PH_FREE) st.phase = JB_PH_DONE;
       break;
     }
+    // Eq. stability every step: the early-warning margin
+    refresh_frames(D, E);
+    st.margin = support_margin_warp(D, E);
+    st.min_margin = fminf(st.min_margin, st.margin);
+    if (st.margin < 0.f && st.first_unstable < 0) st.first_unstable = st.steps;
     if (mode != kModeProtocol) continue;
 
-    refresh_frames(D, E);
     int skip = st.phase == JB_PH_PUSH ? st.pb : -1;
     Terms t = collapse_terms(D, E, skip);
     bool coll = t.dxr > D.P.fall_frac && t.ek > D.P.collapse_ek && t.cmin < D.P.collapse_cos;
     if ((st.phase == JB_PH_PUSH || st.phase == JB_PH_SETTLE) && coll) {
       st.collapsed = 1;
+      st.collapse_step = st.steps;
       if (st.phase == JB_PH_PUSH) end_push(D, E, st);
       st.pb = -1;
       st.phase = JB_PH_REST;
@@ -1812,6 +1916,9 @@ __global__ void init_episodes_kernel(Dev D) {
   memset(&s, 0, sizeof s);
   s.phase = JB_PH_FREE;
   s.pb = -1;
+  s.min_margin = FLT_MAX;
+  s.first_unstable = -1;
+  s.collapse_step = -1;
   D.ep[e] = s;
 }
 
@@ -1864,6 +1971,9 @@ __global__ void protocol_start_kernel(Dev D) {
   s.pb = -1;
   s.collapsed = 0;
   s.resting = 0;
+  s.min_margin = FLT_MAX;
+  s.first_unstable = -1;
+  s.collapse_step = -1;
   int m0 = D.mv_off[e], nm = D.mv_off[e + 1] - m0;
   if (nm <= 0) { s.phase = JB_PH_DONE; D.ep[e] = s; return; }
   int blk = D.mv_block[m0];
@@ -2025,6 +2135,10 @@ __global__ void stats_kernel(Dev D, jb_episode_stats* out) {
   o.pair_steps = st.pair_steps;
   o.bp_tests = st.bp_tests;
   o.mlp_points = st.mlp_points;
+  o.stability_margin = st.steps > 0 ? st.margin : 0.f;
+  o.min_stability_margin = st.steps > 0 ? st.min_margin : 0.f;
+  o.first_unstable_step = st.first_unstable;
+  o.collapse_step = st.collapse_step;
   out[e] = o;
 }
 

@@ -117,10 +117,16 @@ def collect(scene, prot, params, capacity, every=1, max_steps=1 << 30, device="c
 
 def train(rows, epochs=30, batch=8192, lr=3e-4, wd=1e-4, val_frac=0.2, seed=0, device="cuda", log=None):
     """AdamW with cosine decay to lr / 20 over `epochs` (the paper's training
-    recipe, Sec. 9.6), 80/20 split of the rows in recorded order; minibatches
-    are contiguous slices from a per-epoch random offset."""
+    recipe, Sec. 9.6), 80/20 split of the rows at random (seeded permutation,
+    so training and validation rows come from the same episodes and steps);
+    minibatches are contiguous slices of the shuffled training rows from a
+    per-epoch random offset.  The reported training loss is over a random
+    65,536-row sample of the training rows."""
+    import torch
     n = rows.shape[0]
     n_val = int(n * val_frac)
+    perm = torch.from_numpy(np.random.default_rng(seed + 1).permutation(n)).to(rows.device)
+    rows = rows[perm]
     tr, va = rows[: n - n_val], rows[n - n_val:]
     x_tr, t_tr = tr[:, :N_IN].contiguous(), tr[:, N_IN:].contiguous()
     x_va, t_va = va[:, :N_IN].contiguous(), va[:, N_IN:].contiguous()

@@ -182,10 +182,22 @@ def _protocol(moves, n_episodes) -> Protocol:
                     col(6, np.int32), col(7, np.int32))
 
 
-def removal_protocol(towers, seed, push_steps=120, settle_steps=240, max_removals=8):
+def threshold_k(slot, axis, rule="axis"):
+    """The Sec. 5 threshold multiplier k of a push (F = k mu_s m g).
+    rule "axis": 3 along block Y, 4 along block X, whatever the slot (the
+    friction workload's schedule).  rule "ziglar": Tab. ziglar's move
+    classes: side_yaxis and center_xaxis 3, side_xaxis 4 (the torque move);
+    a centre block pulled along Y meets the same friction as along X (its own
+    weight and the layer above on the layer below), so 3 as well."""
+    if rule == "ziglar":
+        return 4.0 if (axis == AXIS_X and slot != 1) else 3.0
+    return 3.0 if axis == AXIS_Y else 4.0
+
+
+def removal_protocol(towers, seed, push_steps=120, settle_steps=240, max_removals=8, k_rule="axis"):
     """Removal rounds: 1..max_removals removals of non-top blocks, each pushed
-    along block X or Y at factor ~ U[0.8, 1.5] of the threshold, then deleted,
-    then a settle period."""
+    along block X or Y at factor ~ U[0.8, 1.5] of the threshold (threshold_k
+    with k_rule), then deleted, then a settle period."""
     moves = []
     for e, t in enumerate(towers):
         n_rem = 1 + int(u01(seed, e, S_NREM, 0) * max_removals)
@@ -199,7 +211,7 @@ def removal_protocol(towers, seed, push_steps=120, settle_steps=240, max_removal
             axis = AXIS_X if u01(seed, e, S_AXIS, r) < 0.5 else AXIS_Y
             sign = 1.0 if u01(seed, e, S_SIGN, r) < 0.5 else -1.0
             factor = 0.8 + 0.7 * float(u01(seed, e, S_FORCE, r))
-            k = 3.0 if axis == AXIS_Y else 4.0
+            k = threshold_k(blk % t.per_level, axis, k_rule)
             ms.append((blk, axis, sign, factor, k, 1, push_steps, settle_steps))
         moves.append(ms)
     return _protocol(moves, len(towers))
@@ -234,11 +246,30 @@ def single_push_workload(seed=0):
     return scene, prot, params(pgs_iters=20)
 
 
-def friction_workload(seed=1, per_mu=150, mus=(0.25, 0.40, 0.60)):
+def ziglar_x_rig(mu, dims=(0.075, 0.025, 0.015), mass=0.015, n=1):
+    """The top two levels of a tower on a static base (Sec. 5.3's X-axis
+    withdrawal): level 0 static (mass 0) along world Y, level 1 (the pushed
+    level, bodies 3-5, body 3 the side block at y = -W) along world X, level
+    2 (bodies 6-8) along world Y; exact masses (no jitter), mu on every block
+    and the ground.  n copies as n episodes."""
+    L, W, H = dims
+    qy = (float(np.cos(np.pi / 4)), 0.0, 0.0, float(np.sin(np.pi / 4)))
+    boxes = []
+    for s in range(3):
+        boxes.append(dict(half=(L / 2, W / 2, H / 2), x=((s - 1) * W, 0.0, H / 2), q=qy, mass=0.0, mu=mu))
+    for s in range(3):
+        boxes.append(dict(half=(L / 2, W / 2, H / 2), x=(0.0, (s - 1) * W, 1.5 * H), mass=mass, mu=mu))
+    for s in range(3):
+        boxes.append(dict(half=(L / 2, W / 2, H / 2), x=((s - 1) * W, 0.0, 2.5 * H), q=qy, mass=mass, mu=mu))
+    one = custom_scene(boxes, ground_mu=mu)
+    return one if n == 1 else concat_scenes([one] * n)
+
+
+def friction_workload(seed=1, per_mu=150, mus=(0.25, 0.40, 0.60), k_rule="axis"):
     """450 episodes (150 per mu), 18 levels, removal rounds, 30 sweeps (mode F)
-    or residual mode."""
+    or residual mode; k_rule as in threshold_k."""
     towers = [Tower(mu=m) for m in mus for _ in range(per_mu)]
-    return build_scene(towers, seed), removal_protocol(towers, seed), params(pgs_iters=30)
+    return build_scene(towers, seed), removal_protocol(towers, seed, k_rule=k_rule), params(pgs_iters=30)
 
 
 def ragged_workload(seed=2, n=4096):
@@ -267,9 +298,9 @@ def stress_workload(seed=5, n=16384):
 
 def subthreshold_workload(seed=11, n=100, levels=6, push_steps=60, settle_steps=120):
     """n towers, mu ~ U[0.25, 0.6]; one push of the middle block of a level in
-    1..levels-2 along block Y (k = 3) or X (k = 4) at factor ~ U[0.5, 0.9]
-    of the threshold, not removed.  Below the thresholds nothing should
-    slide out or topple."""
+    1..levels-2 along block Y or X at factor ~ U[0.5, 0.9] of its Tab. ziglar
+    threshold (a centre block: k = 3 on either axis), not removed.  Below the
+    thresholds nothing should slide out or topple."""
     towers, moves = [], []
     for e in range(n):
         mu = 0.25 + 0.35 * float(u01(seed, e, S_MU, 0))
@@ -278,7 +309,7 @@ def subthreshold_workload(seed=11, n=100, levels=6, push_steps=60, settle_steps=
         axis = AXIS_X if u01(seed, e, S_AXIS, 0) < 0.5 else AXIS_Y
         sign = 1.0 if u01(seed, e, S_SIGN, 0) < 0.5 else -1.0
         factor = 0.5 + 0.4 * float(u01(seed, e, S_FORCE, 0))
-        k = 3.0 if axis == AXIS_Y else 4.0
+        k = threshold_k(1, axis, "ziglar")
         moves.append([(3 * lev + 1, axis, sign, factor, k, 0, push_steps, settle_steps)])
     return build_scene(towers, seed), _protocol(moves, n), params(residual_tol=1e-5, pgs_iter_cap=20000)
 
