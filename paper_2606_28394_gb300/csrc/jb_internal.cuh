@@ -156,6 +156,7 @@ __host__ __device__ inline SmemPlan smem_plan(int nb_max, int pc_max, int ps) {
   s.off_mask = o; o += 8 * s.nbs;
   s.off_f = o; o += 4 * kBodyStride * s.nbs;
   s.off_flags = o; o += 4 * s.nbs;
+  o = (o + 15) & ~15;   // the candidate array is reused for float2 corner lists
   s.off_cand = o; o += 4 * cand_capacity(nb_max);
   s.off_col = o; o += 4 * 3 * (kMaxColours + 1);
   o = (o + 15) & ~15;
