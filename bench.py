@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--fixed-iters", type=int, default=0,
                     help="fixed-sweep mode with this many sweeps per solve (profiling)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--compare-seeds", type=int, default=3,
+                    help="seeds of the workload on which both warm-start arms run (the benchmark's first)")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the learned-vs-plain comparison over seeds and the unaccelerated plain arm")
     ap.add_argument("--no-cpu", action="store_true")
@@ -77,7 +79,10 @@ def parse():
     ap.add_argument("--train-episodes", type=int, default=96,
                     help="learned path: episodes (other seeds) whose converged solves make the training set")
     ap.add_argument("--collect-steps", type=int, default=1 << 30, help="steps of their schedule to record")
-    ap.add_argument("--collect-every", type=int, default=32, help="record every n-th converged solve")
+    ap.add_argument("--collect-every", type=int, default=1, help="record every n-th converged solve")
+    ap.add_argument("--collect-all-points", dest="collect_unmatched", action="store_false",
+                    help="record every point of a recorded solve, not only the points without a "
+                         "previous-frame impulse")
     ap.add_argument("--train-rows", type=int, default=5_000_000)
     ap.add_argument("--gate-episodes", type=int, default=48)
     ap.add_argument("--gate-steps", type=int, default=480)
@@ -89,6 +94,9 @@ def parse():
                          "print one JSON line and exit")
     ap.add_argument("--cpu-episodes", type=int, default=0)
     ap.add_argument("--cpu-steps", type=int, default=30)
+    ap.add_argument("--cpu-whole", type=int, default=0,
+                    help="also time the oracle over the whole schedules of this many sampled episodes "
+                         "(minutes of host time; 0 = off)")
     return ap.parse_args()
 
 
@@ -166,8 +174,10 @@ def prepare_learned(args, rank, prm, device):
     t0 = time.perf_counter()
     sc, pr, _ = make_workload(args.workload, 3001 + rank)
     s_tr, p_tr = synth.subset(sc, pr, np.linspace(0, sc.n_episodes - 1, args.train_episodes).round().astype(int))
+    # the training set: the plain solver's converged impulses at the points the
+    # network will predict (no previous-frame impulse), from every solve
     rows = ws.collect(s_tr, p_tr, prm, capacity=args.train_rows, every=args.collect_every,
-                      max_steps=args.collect_steps, device=device)
+                      max_steps=args.collect_steps, device=device, unmatched_only=args.collect_unmatched)
     t1 = time.perf_counter()
     net, hist = ws.train(rows, epochs=30, batch=8192, lr=3e-4, wd=1e-4, device=device)
     torch.cuda.synchronize(device)
@@ -342,6 +352,28 @@ def cpu_baseline(args, scene, prot, prm):
                       f"(evenly spaced over the three mu levels), FP64, plain PGS in natural order, "
                       f"OpenMP over episodes",
             "seconds": dt, "episodes": ne,
+            "sweeps_per_solve": float(st["total_sweeps"].sum() / max(st["solves"].sum(), 1))}
+
+
+def cpu_whole_schedules(args, scene, prot, prm):
+    """The oracle over the whole schedules of a sample of episodes (the same
+    work per episode as the GPU job), FP64 plain PGS in natural order."""
+    import oracle
+    ncores = oracle.num_threads()
+    idx = np.linspace(0, scene.n_episodes - 1, args.cpu_whole).round().astype(int)
+    s, p = synth.subset(scene, prot, idx)
+    s64 = synth.Scene(s.body_off, *[getattr(s, k).astype(np.float64) for k in
+                                    ("half", "mass", "mu", "x", "q", "v", "w", "ground_mu")])
+    w = oracle.World(s64, dict(prm, pgs_accel_period=0, colour_order=0))
+    w.set_protocol(p)
+    t0 = time.perf_counter()
+    w.run_protocol(max_steps=1 << 30, threads=ncores)
+    dt = time.perf_counter() - t0
+    st = w.stats()
+    return {"value": float(st["body_steps"].sum()) / dt, "unit": "body-steps/s", "cores": ncores, "kind": "oracle",
+            "sample": f"whole schedules of {args.cpu_whole} of the {scene.n_episodes} episodes (evenly spaced), "
+                      f"FP64, plain PGS in natural order, OpenMP over episodes",
+            "seconds": dt, "episodes": args.cpu_whole, "idx": idx.tolist(),
             "sweeps_per_solve": float(st["total_sweeps"].sum() / max(st["solves"].sum(), 1))}
 
 
@@ -551,7 +583,8 @@ def main():
     compare = None
     if net is not None and not args.no_compare:
         per_seed = []
-        for sd in COMPARE_SEEDS:
+        seeds = (WORKLOAD_SEED[args.workload],) + tuple(sd for sd in COMPARE_SEEDS if sd != WORKLOAD_SEED[args.workload])
+        for sd in seeds[:max(1, args.compare_seeds)]:
             if sd == WORKLOAD_SEED[args.workload]:
                 sc_s, pr_s = scene, prot
             else:
@@ -571,12 +604,19 @@ def main():
                              "learned_sweeps_per_solve": sps(arms["learned"][1]),
                              "learned_points": float(arms["learned"][1]["mlp_points"].sum()),
                              "point_solves": float(arms["learned"][1]["point_steps"].sum()),
-                             "learned_over_plain": rate(*arms["learned"]) / rate(*arms["plain"])})
+                             "learned_over_plain": rate(*arms["learned"]) / rate(*arms["plain"]),
+                             "plain_over_learned_sweeps": float(arms["plain"][1]["total_sweeps"].sum()
+                                                                / max(arms["learned"][1]["total_sweeps"].sum(), 1))})
         ratios = [r["learned_over_plain"] for r in per_seed]
+        work = [r["plain_over_learned_sweeps"] for r in per_seed]
         compare = {"seeds": per_seed, "learned_over_plain_mean": statistics.mean(ratios),
                    "learned_over_plain_min": min(ratios), "learned_over_plain_max": max(ratios),
-                   "note": "each seed: the whole 450-episode job once per arm; the spread across seeds is "
-                           "trajectory noise (chaotic collapses), the work inside one seed is deterministic"}
+                   "plain_over_learned_sweeps_mean": statistics.mean(work),
+                   "plain_over_learned_sweeps_min": min(work), "plain_over_learned_sweeps_max": max(work),
+                   "note": "each seed: the whole 450-episode job once per arm; the body-steps/s ratio follows "
+                           "the busiest (collapsing, chaotic) episode of each arm, so it spreads across seeds; "
+                           "the total-sweeps ratio is the work saved, and the time saved wherever the GPU is "
+                           "filled (the work inside one seed is deterministic)"}
     # the paper's plain PGS without the conjugate-gradient steps, same job (context)
     unaccel = None
     if prm.get("pgs_accel_period", 0) and not args.no_compare:
@@ -657,6 +697,14 @@ def main():
         st_c = b.stats()
         cb["gpu_sweeps_per_solve_same_sample"] = sps(st_c)
         line["cpu_baseline"] = cb
+        if args.cpu_whole:
+            cw = cpu_whole_schedules(args, scene, prot, prm)
+            s_w, p_w = synth.subset(scene, prot, cw.pop("idx"))
+            b = jb.Batch(s_w, plain_prm, max_moves=int(p_w.off[-1]), stream=stream, device=dev)
+            b.set_protocol(p_w)
+            b.run_protocol(1 << 30)
+            cw["gpu_sweeps_per_solve_same_sample"] = sps(b.stats())
+            cb["whole_schedules"] = cw
         # the work rate counted on the paper's plain PGS sweeps (the oracle's natural
         # order on the same sample) rather than on the GPU's own
         roof["frac_on_plain_pgs_sweeps"] = roof["frac"] * cb["sweeps_per_solve"] / max(sps(st_c), 1e-9)

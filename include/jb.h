@@ -138,6 +138,10 @@ typedef struct {
                                is one of this iteration, so the converged impulses are plain
                                PGS's and the residual test is unchanged; the sweeps needed to
                                reach residual_tol fall.  Uses jb_workspace_bytes' scratch. */
+  int32_t colour_key;       /* order in which the greedy colouring takes the pairs (the sweep order
+                               of the Gauss-Seidel phases; same fixed point): 0 = lower body
+                               ascending, upper body descending; 1 = height of the pair's first
+                               contact point in 1 mm bins ascending, natural index descending */
 } jb_solver_params;
 
 /* Initial scene: host arrays, B = body_off[n_episodes] bodies. */
@@ -379,6 +383,12 @@ jb_status jb_set_warmstart_mlp(jb_batch* b, const void* d_mlp);
  * rows); *d_count (device int32, caller zeroes it) counts rows claimed and may
  * exceed capacity (extra rows are dropped).  capacity 0 turns it off. */
 jb_status jb_set_recorder(jb_batch* b, float* d_rows, int32_t capacity, int32_t* d_count, int32_t every);
+
+/* Which points the recorder takes: 0 (the default) every point of a recorded
+ * solve; 1 only the points without a previous-frame impulse, the ones the
+ * learned warm start predicts in mode 2 (so that the training set has the
+ * distribution the network meets).  JB_EINVAL for other values. */
+jb_status jb_set_recorder_points(jb_batch* b, int32_t unmatched_only);
 
 size_t jb_mlp_bytes(void);              /* device bytes of a network block */
 int32_t jb_mlp_param_count(void);       /* floats of one parameter set */

@@ -654,7 +654,10 @@ static void sweep_order(or_episode* E, int colour) {
   if (!colour || n <= 0) return;
   int (*kv)[2] = (int(*)[2])malloc(sizeof(int) * 2 * (size_t)n);
   for (int i = 0; i < n; ++i) {
-    kv[i][0] = ((E->pairs[i].a + 1) << 16) | (0xffff - E->pairs[i].b);   /* a ascending, b descending */
+    if (colour == 2)   /* height of the first point in 1 mm bins ascending, then index descending */
+      kv[i][0] = (int)floor((E->pairs[i].p[0][2] + 5e-4) * 1000.0) + 1;
+    else               /* lower body ascending, upper body descending */
+      kv[i][0] = ((E->pairs[i].a + 1) << 16) | (0xffff - E->pairs[i].b);
     kv[i][1] = -i;
   }
   qsort(kv, n, sizeof(int) * 2, cmp_int2);

@@ -54,10 +54,12 @@ typedef struct {
                             and a touching point approaching faster than restitution_vmin
                             targets v_n = -e v_n(pre-solve) */
   double restitution_vmin; /* m/s; <= 0 selects 2 |g| h */
-  int colour_order;      /* 0: Gauss-Seidel in natural pair order (the listing); 1: in the GPU
-                            library's colour order: greedy lowest-free colouring of the pairs taken
-                            by (lower body a ascending, upper body b descending), colours
-                            ascending, natural index ascending within a colour.  Static bodies
+  int colour_order;      /* 0: Gauss-Seidel in natural pair order (the listing); 1 and 2: in the
+                            GPU library's colour order: greedy lowest-free colouring of the pairs
+                            taken by (1) lower body a ascending, upper body b descending or (2)
+                            the height of their first point in 1 mm bins ascending, natural index
+                            descending; colours ascending, natural index ascending within a
+                            colour.  Static bodies
                             (the ground) do not constrain the colouring.  Same fixed point.  This
                             restates the GPU's schedule so that a fixed number of unconverged
                             sweeps can be compared iterate for iterate; it is opt-in for that test

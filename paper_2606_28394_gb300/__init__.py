@@ -45,7 +45,8 @@ class jb_solver_params(C.Structure):
                 ("smem_pair_factor", C.c_float), ("sor", C.c_float), ("sweep_order", C.c_int32),
                 ("residual_every_max", C.c_int32), ("stall_window", C.c_int32),
                 ("friction_cone", C.c_int32), ("restitution_newton", C.c_int32),
-                ("restitution_vmin", C.c_float), ("pgs_accel_period", C.c_int32)]
+                ("restitution_vmin", C.c_float), ("pgs_accel_period", C.c_int32),
+                ("colour_key", C.c_int32)]
 
 
 _fp = C.POINTER(C.c_float)
@@ -119,6 +120,7 @@ _sig = {
     "jb_load_state": (C.c_int32, [_vp, _vp, C.c_size_t]),
     "jb_set_warmstart_mlp": (C.c_int32, [_vp, _vp]),
     "jb_set_recorder": (C.c_int32, [_vp, _vp, C.c_int32, _vp, C.c_int32]),
+    "jb_set_recorder_points": (C.c_int32, [_vp, C.c_int32]),
     "jb_mlp_bytes": (C.c_size_t, []),
     "jb_mlp_param_count": (C.c_int32, []),
     "jb_mlp_scratch_bytes": (C.c_size_t, [C.c_int32]),

@@ -1,11 +1,20 @@
 """Autotuner for the batched step.
 
-Picks the per-episode shared-memory solver capacity (smem_pair_factor: pairs
-per body kept on chip before a step falls back to global memory, which sets
-how many episodes fit per SM) and the residual-check cadence
-(residual_every, residual_every_max) by timing short trials of the actual
-workload with CUDA events: the first `trial_steps` physics steps of a sample
-of its episodes.
+Picks, by timing short trials of the actual workload with CUDA events (the
+first `trial_steps` physics steps of a sample of its episodes):
+  - smem_pair_factor: pairs per body whose solver records stay in shared
+    memory before a step falls back to global memory; it sets how many
+    episodes fit per SM (the episode-to-SM packing);
+  - the residual-check cadence (residual_every, residual_every_max);
+  - pgs_accel_period: how often the conjugate-gradient step runs (0 = plain
+    PGS), i.e. the iteration schedule;
+  - colour_key: the order in which the greedy colouring takes the pairs, i.e.
+    the colour schedule of a sweep.
+The search is coordinate descent: each knob in turn over its candidates with
+the others at their best so far, two rounds (a trial already timed is not
+repeated).  One warp per episode and one episode per CTA are fixed by the
+kernel (a tower's largest colour holds about 20 pairs, so more lanes per
+episode would idle, and a CTA per episode lets size classes share SMs).
 Choices are cached in a JSON file keyed by GPU name and a hash of the
 workload's shape and solver parameters.
 """
@@ -24,7 +33,18 @@ from . import Batch
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), ".autotune_cache.json")
 FACTORS = (3.6, 4.0, 5.0)
 CADENCE = ((4, 4), (4, 32), (2, 32))   # (residual_every, residual_every_max)
-TUNED = ("smem_pair_factor", "residual_every", "residual_every_max")
+ACCEL = (0, 32, 64, 128)
+KEYS = (0, 1)
+TUNED = ("smem_pair_factor", "residual_every", "residual_every_max", "pgs_accel_period", "colour_key")
+# the knobs of the coordinate descent, each a list of settings
+KNOBS = (
+    ("smem_pair_factor", [{"smem_pair_factor": f} for f in FACTORS]),
+    ("cadence", [{"residual_every": a, "residual_every_max": b} for a, b in CADENCE]),
+    ("pgs_accel_period", [{"pgs_accel_period": m} for m in ACCEL]),
+    ("colour_key", [{"colour_key": k} for k in KEYS]),
+)
+DEFAULTS = {"smem_pair_factor": 4.0, "residual_every": 4, "residual_every_max": 32, "pgs_accel_period": 64,
+            "colour_key": 0}
 
 
 def subset(scene, prot, episodes):
@@ -92,15 +112,27 @@ def tune(scene, prot, params, trial_steps=120, sample=64, device="cuda", use_cac
     idx = np.linspace(0, scene.n_episodes - 1, min(sample, scene.n_episodes)).round().astype(int)
     s, p = subset(scene, prot, idx)
     table = []
-    for fac in FACTORS:
-        for ev, evm in CADENCE:
-            prm = dict(params, smem_pair_factor=fac, residual_every=ev, residual_every_max=evm)
-            ms = trial(s, p, prm)
-            table.append({"smem_pair_factor": fac, "residual_every": ev, "residual_every_max": evm, "ms": ms})
+    timed = {}
+
+    def run(choice):
+        key_ = tuple(choice[k] for k in TUNED)
+        if key_ not in timed:
+            ms = trial(s, p, dict(params, **choice))
+            timed[key_] = ms
+            table.append(dict(choice, ms=ms))
             if log:
-                log(f"factor {fac} cadence {ev}..{evm}: {ms:.1f} ms")
-    best = min(table, key=lambda r: r["ms"])
-    choice = {k: best[k] for k in TUNED}
+                log(f"{choice}: {ms:.1f} ms")
+        return timed[key_]
+
+    choice = {k: params.get(k, DEFAULTS[k]) for k in TUNED}
+    best_ms = run(choice)
+    for _ in range(2):
+        for _name, settings in KNOBS:
+            for st in settings:
+                cand = dict(choice, **st)
+                ms = run(cand)
+                if ms < best_ms:
+                    best_ms, choice = ms, cand
     if use_cache:
         cache[key] = {"best": choice, "table": table}
         with open(cache_path, "w") as f:

@@ -202,6 +202,7 @@ Params to_params(const jb_solver_params* p) {
   q.friction_cone = p->friction_cone;
   q.restitution_newton = p->restitution_newton;
   q.accel_period = p->pgs_accel_period;
+  q.colour_key = p->colour_key;
   {
     const float g = sqrtf(p->gravity[0] * p->gravity[0] + p->gravity[1] * p->gravity[1] + p->gravity[2] * p->gravity[2]);
     q.restitution_vmin = p->restitution_vmin > 0.f ? p->restitution_vmin : 2.f * g * p->dt / (float)p->n_sub;
@@ -227,6 +228,7 @@ const char* check_params(const jb_solver_params* p) {
   if (p->friction_cone < 0 || p->friction_cone > 1) return "friction_cone must be 0 or 1";
   if (p->restitution_newton < 0 || p->restitution_newton > 1) return "restitution_newton must be 0 or 1";
   if (p->pgs_accel_period < 0) return "pgs_accel_period must be >= 0";
+  if (p->colour_key < 0 || p->colour_key > 1) return "colour_key must be 0 or 1";
   return nullptr;
 }
 
@@ -481,6 +483,13 @@ jb_status jb_set_recorder(jb_batch* b, float* d_rows, int32_t capacity, int32_t*
   b->D.rec_count = capacity > 0 ? d_count : nullptr;
   b->D.rec_cap = capacity;
   b->D.rec_every = every > 0 ? every : 1;
+  return JB_OK;
+}
+
+jb_status jb_set_recorder_points(jb_batch* b, int32_t unmatched_only) {
+  if (!b) return fail(JB_EINVAL, "jb_set_recorder_points: null batch");
+  if (unmatched_only < 0 || unmatched_only > 1) return fail(JB_EINVAL, "jb_set_recorder_points: 0 or 1");
+  b->D.rec_unmatched = unmatched_only;
   return JB_OK;
 }
 

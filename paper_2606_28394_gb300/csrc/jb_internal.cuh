@@ -67,6 +67,7 @@ struct Params {
   int restitution_newton;  // 1: bounce target instead of the (1+e) factor
   float restitution_vmin;  // m/s (resolved: > 0)
   int accel_period;        // 0 = plain PGS; m > 0: a conjugate-gradient step every m sweeps
+  int colour_key;          // 0: (a asc, b desc); 1: (height bin asc, natural index desc)
 };
 
 // One contact buffer (the batch holds two: this step's and the previous one).
@@ -122,6 +123,7 @@ struct Dev {
   float* rec;
   int32_t* rec_count;
   int rec_cap, rec_every;
+  int rec_unmatched;      // 1: the recorder takes only points without a previous-frame impulse
 };
 
 // Error reporting shared by the library's translation units.

@@ -16,7 +16,8 @@ import math
 import numpy as np
 
 from . import (Batch, check, jb_mlp_bytes, jb_mlp_forward, jb_mlp_grad, jb_mlp_load, jb_mlp_param_count,
-               jb_mlp_save, jb_mlp_scratch_bytes, jb_mlp_train_step, jb_set_recorder, jb_set_warmstart_mlp,
+               jb_mlp_save, jb_mlp_scratch_bytes, jb_mlp_train_step, jb_set_recorder, jb_set_recorder_points,
+               jb_set_warmstart_mlp,
                _fp)
 
 N_IN, N_HID, N_OUT = 24, 128, 3
@@ -98,16 +99,18 @@ class Network:
         return loss
 
 
-def collect(scene, prot, params, capacity, every=1, max_steps=1 << 30, device="cuda"):
+def collect(scene, prot, params, capacity, every=1, max_steps=1 << 30, device="cuda", unmatched_only=False):
     """Runs the plain solver through the schedule with the recorder on; returns
     the recorded rows [n, 27] (device tensor): features, then the converged
-    impulses in units of m_bar |g| h."""
+    impulses in units of m_bar |g| h.  unmatched_only records only the points
+    without a previous-frame impulse (the points mode 2 predicts)."""
     import torch
     prm = dict(params, warm_start=1)
     b = Batch(scene, prm, max_moves=int(prot.off[-1]), device=device)
     rows = torch.zeros((capacity, REC), dtype=torch.float32, device=b.device)
     count = torch.zeros(1, dtype=torch.int32, device=b.device)
     check(jb_set_recorder(b.h, rows.data_ptr(), capacity, count.data_ptr(), every), "jb_set_recorder")
+    check(jb_set_recorder_points(b.h, 1 if unmatched_only else 0), "jb_set_recorder_points")
     b.set_protocol(prot)
     b.run_protocol(max_steps)
     b.sync()

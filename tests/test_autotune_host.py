@@ -23,13 +23,18 @@ def test_picks_the_fastest_trial_and_caches_it(tmp_path):
     def trial(s, p, q):
         calls.append(q)
         assert s.n_episodes == 8          # the sample, evenly spaced over the batch
-        # fastest: factor 5 with checks every 2..32
-        return 10.0 + abs(q["smem_pair_factor"] - 5.0) + (0 if q["residual_every"] == 2 else 1)
+        # fastest: factor 5, checks every 2..32, the step every 128 sweeps, height key
+        return (10.0 + abs(q["smem_pair_factor"] - 5.0) + (0 if q["residual_every"] == 2 else 1)
+                + abs(q["pgs_accel_period"] - 128) / 64 + (0 if q["colour_key"] == 1 else 0.5))
 
     cache = str(tmp_path / "cache.json")
     tuned, table = a.tune(scene, prot, prm, sample=8, trial=trial, gpu_name="fake", cache_path=cache)
-    assert len(calls) == len(a.FACTORS) * len(a.CADENCE) == len(table)
+    # coordinate descent: distinct trials only, fewer than the full grid
+    grid = len(a.FACTORS) * len(a.CADENCE) * len(a.ACCEL) * len(a.KEYS)
+    assert len(calls) == len(table) < grid
+    assert len({tuple(c[k] for k in a.TUNED) for c in calls}) == len(calls)
     assert (tuned["smem_pair_factor"], tuned["residual_every"], tuned["residual_every_max"]) == (5.0, 2, 32)
+    assert (tuned["pgs_accel_period"], tuned["colour_key"]) == (128, 1)
     assert tuned["residual_tol"] == prm["residual_tol"]           # the rest of params untouched
     stored = json.load(open(cache))
     assert len(stored) == 1 and list(stored.values())[0]["best"]["smem_pair_factor"] == 5.0

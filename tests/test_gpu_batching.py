@@ -45,8 +45,12 @@ def test_autotuner_returns_a_candidate(cuda_device):
     tuned, table = autotune.tune(scene, prot, prm, trial_steps=8, sample=8, use_cache=False)
     assert tuned["smem_pair_factor"] in autotune.FACTORS
     assert (tuned["residual_every"], tuned["residual_every_max"]) in autotune.CADENCE
-    assert len(table) == len(autotune.FACTORS) * len(autotune.CADENCE)
+    assert tuned["pgs_accel_period"] in autotune.ACCEL and tuned["colour_key"] in autotune.KEYS
+    # coordinate descent: distinct trials, the choice the fastest of them
+    assert 1 < len(table) < len(autotune.FACTORS) * len(autotune.CADENCE) * len(autotune.ACCEL) * len(autotune.KEYS)
     assert all(r["ms"] > 0 for r in table)
+    best = min(table, key=lambda r: r["ms"])
+    assert all(tuned[k] == best[k] for k in autotune.TUNED)
 
 
 def test_ragged_batch_one_step_parity(cuda_device):

@@ -181,3 +181,34 @@ def test_trained_network_gains_on_cold_contacts(cuda_device):
     plain, learned, gain = ws().cold_start_gain(s_ev, prm, net, steps=12)
     print(f"cold contacts: plain {plain:.0f}, learned {learned:.0f} sweeps per solve (gain {gain:.2f})")
     assert gain > 1.1, (plain, learned)
+
+
+def test_trained_network_against_plain_pgs_on_fresh_towers(cuda_device):
+    """The learned warm start against the method without it, plain PGS with
+    previous-frame warm start, on the same episodes: the first 24 steps of
+    removal-round towers of fresh seeds, solved as the benchmark solves
+    (residual 1e-5, the conjugate-gradient step every 64 sweeps).  Both arms
+    start every persisting point from its previous impulse; they differ only
+    at points without one (every point of the first step, new contacts
+    later), where plain PGS starts from zero and the learned arm from the
+    network trained on the plain solver's converged impulses at such points
+    (other seeds).  Both reach the residual on every solve, and the learned
+    arm's sweeps per solve stay within 5 % of plain PGS's: with the
+    conjugate-gradient step a cold start costs the plain arm little, and the
+    points without a previous impulse are a small share of the point-solves,
+    so what the network gains here is within the run-to-run variation of its
+    training (the weight-gradient kernel's atomic split-K sums make training
+    runs differ); where it acts on every point it gains clearly
+    (test_trained_network_gains_on_cold_contacts)."""
+    sc, pr, prm = synth.friction_workload(seed=3001)
+    prm = dict(prm, residual_tol=1e-5, pgs_iter_cap=20000, pgs_accel_period=64)
+    s_tr, p_tr = synth.subset(sc, pr, range(0, 450, 15))
+    rows = ws().collect(s_tr, p_tr, prm, capacity=400000, every=1, max_steps=240, unmatched_only=True)
+    assert rows.shape[0] > 1000 and (rows[:, 22] == 0).all()
+    net, _ = ws().train(rows, epochs=30, batch=8192, lr=1e-3, seed=0)
+    ev, pev, _ = synth.friction_workload(seed=4001)
+    s_ev, p_ev = synth.subset(ev, pev, range(0, 450, 10))
+    out = ws().evaluate(s_ev, p_ev, prm, net, mode=2, max_steps=24)
+    print("fresh towers, 24 steps:", out["plain"]["sweeps_per_solve"], out["learned"]["sweeps_per_solve"], out["gain"])
+    assert out["plain"]["not_converged"] == 0 and out["learned"]["not_converged"] == 0
+    assert out["gain"] > 0.95, out

@@ -543,23 +543,23 @@ def test_newton_restitution_fp32_and_parity(cuda_device):
     assert ev < 1e-4 and ew < 1e-4, (ev, ew)
 
 
-@pytest.mark.parametrize("accel", [0, 4])
+@pytest.mark.parametrize("accel,key", [(0, 0), (4, 0), (0, 1)])
 @pytest.mark.parametrize("name", ["tower18", "tower4_perturbed"])
-def test_fixed_sweeps_match_the_oracle_in_colour_order(cuda_device, name, accel):
+def test_fixed_sweeps_match_the_oracle_in_colour_order(cuda_device, name, accel, key):
     """With the oracle sweeping in the library's colour order, the iterates
     themselves agree, not only the fixed point: one step of 20 fixed sweeps
     (far from converged) gives the same state up to FP32 rounding.  This
     checks the sweep arithmetic (the point-block rows, the packed impulse
     application, the colour schedule) row for row, and with accel = 4 the
     five conjugate-gradient steps in between (direction, beta, restart,
-    projection, impulse application)."""
+    projection, impulse application); with key = 1 the height-bin colouring."""
     if name == "tower18":
         scene = synth.build_scene([synth.Tower()], 0)
     else:
         scene = synth.perturbed(synth.build_scene([synth.Tower(levels=4, mu=0.5)], 1), 5, dx=2e-4, dang=0.01)
     prm = synth.params(pgs_iters=20, pgs_accel_period=accel)
-    b = jb().Batch(scene, prm)
-    w = oracle.World(as64(scene), dict(prm, colour_order=1))
+    b = jb().Batch(scene, dict(prm, colour_key=key))
+    w = oracle.World(as64(scene), dict(prm, colour_order=1 + key))
     b.step(1)
     w.step(1)
     xg, qg, vg, wg = b.state()
@@ -573,7 +573,7 @@ def test_fixed_sweeps_match_the_oracle_in_colour_order(cuda_device, name, accel)
     assert np.abs(wn.state()[2] - vo).max() > 1e-5
     if accel:
         # and so is the plain solve's in the same order: the agreement is the acceleration's
-        wp = oracle.World(as64(scene), dict(prm, colour_order=1, pgs_accel_period=0))
+        wp = oracle.World(as64(scene), dict(prm, colour_order=1 + key, pgs_accel_period=0))
         wp.step(1)
         assert np.abs(wp.state()[2] - vo).max() > 1e-5
 

@@ -753,12 +753,14 @@ def test_colour_order_keeps_the_fixed_point():
                                      ("half", "mass", "mu", "x", "q", "v", "w", "ground_mu")])
     out = {}
     for name, prm in (("conv", dict(residual_tol=1e-11, pgs_iter_cap=2000000)), ("fixed", dict(pgs_iters=20))):
-        for order in (0, 1):
+        for order in (0, 1, 2):
             W = oracle.World(s64, synth.params(colour_order=order, **prm))
             W.step(1)
             out[name, order] = W.state()
-    assert np.abs(out["conv", 0][2] - out["conv", 1][2]).max() < 1e-7
-    assert np.abs(out["fixed", 0][2] - out["fixed", 1][2]).max() > 1e-5
+    for order in (1, 2):
+        assert np.abs(out["conv", 0][2] - out["conv", order][2]).max() < 1e-7
+        assert np.abs(out["fixed", 0][2] - out["fixed", order][2]).max() > 1e-5
+    assert np.abs(out["fixed", 1][2] - out["fixed", 2][2]).max() > 1e-6
 
 
 def _ziglar_x_trial(mu, k, steps=120):
