@@ -54,7 +54,7 @@ class _Params(C.Structure):
                 ("collapse_ek", C.c_double), ("collapse_theta_deg", C.c_double),
                 ("rest_ek", C.c_double), ("rest_steps", C.c_int), ("friction_cone", C.c_int),
                 ("restitution_newton", C.c_int), ("restitution_vmin", C.c_double), ("colour_order", C.c_int),
-                ("pgs_accel_period", C.c_int)]
+                ("pgs_accel_period", C.c_int), ("sat_tie", C.c_double)]
 
 
 def lib():

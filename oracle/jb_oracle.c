@@ -187,17 +187,20 @@ static void sat15(const box_t* A, const box_t* B, double delta[15], int valid[15
    micro-radian tilts flip the pair between them (and between 4-point face
    and 1-point edge manifolds) from step to step.  Contact exists iff the
    minimum delta over all valid axes exceeds -margin (speculative contacts). */
-static int sat_select(const double delta[15], const int valid[15], double* dmin_out) {
+static int sat_select_tie(const double delta[15], const int valid[15], double* dmin_out, double tie) {
   double dmin = delta[0];
   for (int k = 1; k < 15; ++k) if (valid[k] && delta[k] < dmin) dmin = delta[k];
   *dmin_out = dmin;
   int bf = 0;
-  for (int k = 1; k < 6; ++k) if (delta[k] < delta[bf] - TIE_ABS) bf = k;
+  for (int k = 1; k < 6; ++k) if (delta[k] < delta[bf] - tie) bf = k;
   int be = -1;
   for (int k = 6; k < 15; ++k)
-    if (valid[k] && (be < 0 || delta[k] < delta[be] - TIE_ABS)) be = k;
-  if (be >= 0 && delta[be] < delta[bf] - (EDGE_REL * fabs(delta[bf]) + TIE_ABS)) return be;
+    if (valid[k] && (be < 0 || delta[k] < delta[be] - tie)) be = k;
+  if (be >= 0 && delta[be] < delta[bf] - (EDGE_REL * fabs(delta[bf]) + tie)) return be;
   return bf;
+}
+static int sat_select(const double delta[15], const int valid[15], double* dmin_out) {
+  return sat_select_tie(delta, valid, dmin_out, TIE_ABS);
 }
 
 /* ------------------------------------------------- Sec. 6.2.1 manifold ----- */
@@ -415,12 +418,16 @@ static int edge_manifold(const box_t* A, const box_t* B, int axis, const double*
 }
 
 /* Box-box narrowphase; returns 1 and fills axis, n, delta, points if in contact. */
+static int box_pair_tie(const box_t* A, const box_t* B, double margin, or_pair* pr, double* dmin_out, double tie);
 static int box_pair(const box_t* A, const box_t* B, double margin, or_pair* pr, double* dmin_out) {
+  return box_pair_tie(A, B, margin, pr, dmin_out, TIE_ABS);
+}
+static int box_pair_tie(const box_t* A, const box_t* B, double margin, or_pair* pr, double* dmin_out, double tie) {
   double delta[15], U[15][3];
   int valid[15];
   sat15(A, B, delta, valid, U);
   double dmin;
-  int ax = sat_select(delta, valid, &dmin);
+  int ax = sat_select_tie(delta, valid, &dmin, tie);
   if (dmin_out) *dmin_out = dmin;
   if (!(dmin > -margin)) return 0;
   double d[3] = {B->x[0] - A->x[0], B->x[1] - A->x[1], B->x[2] - A->x[2]};
@@ -511,7 +518,7 @@ static void detect(or_episode* E, const or_params* P) {
       if (!ov) continue;
       box_t ba, bb; box_of(A, &ba); box_of(B, &bb);
       memset(&pr, 0, sizeof pr);
-      if (box_pair(&ba, &bb, P->contact_margin, &pr, NULL)) {
+      if (box_pair_tie(&ba, &bb, P->contact_margin, &pr, NULL, P->sat_tie > 0 ? P->sat_tie : TIE_ABS)) {
         pr.a = i; pr.b = j;
         pr.mu = fmin(A->mu, B->mu);
         push_pair(E, &pr);

@@ -67,6 +67,8 @@ typedef struct {
   int pgs_accel_period;      /* 0: plain projected Gauss-Seidel (the paper).  m > 0: after every m
                             sweeps one nonsmooth conjugate-gradient step (see solve()); the
                             converged impulses are those of plain PGS. */
+  double sat_tie;        /* SAT axis-choice hysteresis (m); <= 0 selects the default 1e-5 (a later
+                            face axis replaces the best only if smaller by this much) */
 } or_params;
 
 /* episode statistics, one row of OR_NSTAT doubles per episode */

@@ -227,7 +227,7 @@ BASE_PARAMS = dict(dt=1.0 / 240.0, n_sub=1, pgs_iters=20, residual_tol=0.0,
                    fall_frac=0.5, collapse_ek=5e-5, collapse_theta_deg=30.0,
                    rest_ek=1e-7, rest_steps=400, friction_cone=0,
                    restitution_newton=0, restitution_vmin=0.0, colour_order=0,
-                   pgs_accel_period=0)
+                   pgs_accel_period=0, sat_tie=0.0)
 
 
 def params(**kw):

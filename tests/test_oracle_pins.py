@@ -808,6 +808,47 @@ def test_ziglar_x_axis_rig():
         assert _ziglar_x_trial(mu, 4.0)[1] < 1.0
 
 
+def test_sat_hysteresis_changes_only_near_tie_axis_choices():
+    """The SAT axis hysteresis (a later face axis replaces the best only if
+    smaller by the tie band, 10 um by default; 0.1 um tried here) is a
+    reading of Sec. 6.2's "axis of minimum delta".  On a flush tower every
+    tie is exact, so both bands give the same step bit for bit.  On a tower
+    tilted by up to 10 mrad the contact pairs are the same, and every pair
+    whose chosen axis differs between the two bands has its two candidate
+    axes' separations within 10 um of each other (recomputed by the 15-axis
+    SAT), so the band decides only near-ties.  Those choices still matter:
+    the two reference faces clip different manifolds whose depths differ by
+    micrometres, and the speculative bias -depth / h turns that into
+    millimetres per second in the step's velocities; the GPU and the oracle
+    therefore use the same band."""
+    flush = synth.build_scene([synth.Tower(levels=4, mu=0.5)], 1)
+    tilted = synth.perturbed(flush, 5, dx=2e-4, dang=0.01)
+    for name, sc in (("flush", flush), ("tilted", tilted)):
+        s64 = synth.Scene(sc.body_off, *[getattr(sc, k).astype(np.float64) for k in
+                                         ("half", "mass", "mu", "x", "q", "v", "w", "ground_mu")])
+        res = {}
+        for tie in (1e-7, 1e-5):
+            W = oracle.World(s64, synth.params(residual_tol=1e-10, pgs_iter_cap=2000000, sat_tie=tie))
+            W.step(1)
+            res[tie] = (W.state(), {(r["a"], r["b"]): r["axis"] for r in oracle.contact_dicts(W.contacts(0))})
+        (st7, c7), (st5, c5) = res[1e-7], res[1e-5]
+        assert set(c7) == set(c5)
+        if name == "flush":
+            assert c7 == c5 and all(np.array_equal(a, b) for a, b in zip(st7, st5))
+            continue
+        differ = [k for k in c7 if c7[k] != c5[k]]
+        assert differ, "the tilted tower has near-ties"
+        for a, b in differ:
+            o = s64.body_off[0]
+            A = [np.zeros(3), np.array([1.0, 0, 0, 0]), np.array([1e3, 1e3, 1e-3])] if a < 0 else \
+                [s64.x[:, o + a], s64.q[:, o + a], s64.half[:, o + a]]
+            if a < 0:
+                continue    # ground pairs take no face choice
+            r = oracle.sat(*A, s64.x[:, o + b], s64.q[:, o + b], s64.half[:, o + b], margin=1e-3)
+            d = r["delta"]
+            assert abs(d[c7[(a, b)]] - d[c5[(a, b)]]) < 1e-5 + 0.05 * abs(d[c5[(a, b)]]), (a, b, d)
+
+
 def _flush_stack(n, hz=0.0075):
     """n blocks stacked flush on the ground in FP64 (no jitter)."""
     half = np.tile(np.array([[0.0375], [0.0125], [hz]]), (1, n))
