@@ -21,6 +21,7 @@
 // Everything is FP32 (the network's operands BF16).  Waits are warp barriers
 // only; every loop is bounded.
 #include <cfloat>
+#include <climits>
 #include <cstdint>
 
 #include "jb_internal.cuh"
@@ -115,6 +116,7 @@ struct Contact {
   float depth[kMaxPts];
 };
 
+constexpr int kDenseChecks = 6;     // residual checks every sweep over this many sweeps after a CG step
 constexpr float kTieAbs = 1e-5f;    // SAT axis hysteresis (m): keeps near-parallel axis choices stable
 constexpr float kEdgeRel = 0.05f;   // a cross axis must beat the best face axis by 5 %
 constexpr float kCrossEps = 1e-6f;  // degenerate cross axes are skipped
@@ -1447,6 +1449,7 @@ __device__ StepOut substep(const Dev& D, const Ep& E, EpState& st, float h) {
     const int am = Pm.accel_period;
     float* acc = D.acc + E.poff * kAccFloats;
     float r2_prev = 0.f;
+    int dense_from = INT_MAX - kDenseChecks;   // start of the dense-check window after a step
     if (am > 0) accel_begin(V, acc, npairs, lane);
     while (sweeps < cap) {
       colour_passes<1>(V, s.off, ncol, lane, e1om, om, Pm.sweep_order == 1 && (sweeps & 1), Pm.beta, Pm.slop,
@@ -1458,8 +1461,15 @@ __device__ StepOut substep(const Dev& D, const Ep& E, EpState& st, float h) {
         if (!(beta <= 1.f)) beta = 0.f;   // restart (and NaN)
         r2_prev = r2;
         accel_step(V, acc, s.off, ncol, lane, beta, Pm.friction_cone != 0);
+        if (beta > 0.f) dense_from = sweeps + 2;
       }
-      if (sweeps >= next || sweeps == cap) {
+      // a conjugate-gradient step first raises the residual (its
+      // extrapolation overshoots), then the next sweeps bring it to its
+      // lowest for a few sweeps before the plain decay resumes; the checks
+      // run every sweep over that window, which a cadence fitted to the
+      // plain sweeps' geometric decay would step over
+      const bool dense = rmode && sweeps >= dense_from && sweeps < dense_from + kDenseChecks;
+      if (sweeps >= next || sweeps == cap || dense) {
         res = episode_residual(V, npairs, lane, Pm.friction_cone != 0);
         if (!rmode || res <= Pm.residual_tol || !(res == res)) break;
         // stall test: fit res = win_res * exp(rate * sweeps) over the window
