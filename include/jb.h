@@ -360,7 +360,10 @@ jb_status jb_load_state(jb_batch* b, const void* host_buf, size_t bytes);
  * m_bar = 0.015 kg, L_bar = 0.075 m, h the substep):
  *   0-2   relative point velocity of b w.r.t. a along n, t1, t2, times s_v
  *   3     depth / contact_margin
- *   4-9   n, t1
+ *   4-8   n, then t1.x, t1.y (t1.z follows from n by the tangent rule)
+ *   9     height of the episode's column above the point: the highest AABB
+ *         top of its active dynamic blocks minus the point's z, over 0.15 m
+ *         (ten nominal block thicknesses); stands in for the load above
  *   10-11 m_bar / m of a, b (0 for static bodies and the ground)
  *   12-17 body-frame inertia diagonals of a, b over m_bar L_bar^2 (0 if static)
  *   18    friction coefficient
@@ -392,7 +395,13 @@ jb_status jb_set_recorder_points(jb_batch* b, int32_t unmatched_only);
 
 size_t jb_mlp_bytes(void);              /* device bytes of a network block */
 int32_t jb_mlp_param_count(void);       /* floats of one parameter set */
-size_t jb_mlp_scratch_bytes(int32_t n); /* device scratch for n rows */
+/* Device scratch of jb_mlp_forward / jb_mlp_grad / jb_mlp_train_step (the
+ * gradient, the loss and an error flag; the same for every n > 0; 0 for
+ * n <= 0).  The batch forward and the gradient run in one fused kernel on the
+ * tcgen05 tensor cores (BF16 operands in shared memory, FP32 accumulators in
+ * tensor memory), one CTA per 128 rows up to one per SM; the rows and
+ * activations never go to global memory. */
+size_t jb_mlp_scratch_bytes(int32_t n);
 /* Loads parameters (host, jb_mlp_param_count floats, layout above) into the
  * block, zeroes the AdamW moments and packs the BF16 operands. */
 jb_status jb_mlp_load(void* d_mlp, const float* params, void* cuda_stream);
@@ -413,6 +422,12 @@ jb_status jb_mlp_adamw(void* d_mlp, const float* d_grad, int32_t step, float lr,
 jb_status jb_mlp_train_step(void* d_mlp, const float* d_x, const float* d_t, int32_t n, int32_t step, float lr,
                             float beta1, float beta2, float eps, float weight_decay, float* d_loss,
                             void* d_scratch, size_t scratch_bytes, void* cuda_stream);
+/* Synchronises the stream and reads the error flag of the last
+ * jb_mlp_forward / jb_mlp_grad / jb_mlp_train_step that used this scratch:
+ * 1 if a wait of the tensor-core kernel for its own matrix products ran out
+ * (about one second; the kernel then skipped its outputs, freed its tensor
+ * memory and returned), else 0. */
+jb_status jb_mlp_scratch_error(const void* d_scratch, size_t scratch_bytes, void* cuda_stream, int32_t* out);
 
 /* Stepping for callers that cannot allocate device memory.
  *

@@ -923,14 +923,26 @@ static void save_cache(or_episode* E) {
 
 /* Warm-start network inputs of every point (learned warm start, not in the
    paper): pre-solve relative point velocity of B w.r.t. A along n, t1, t2
-   over |g| h; depth over the margin; n; t1; m_bar/m of A and B (0 if
-   static); body inertia diagonals over m_bar L_bar^2 (0 if static); mu;
-   matched previous-frame impulses over m_bar |g| h; matched flag; ground flag. */
+   over |g| h; depth over the margin; n; t1.x, t1.y (t1.z follows from n by
+   the tangent rule); the height of the episode's column above the point
+   (highest AABB top of its active dynamic blocks minus the point's z) over
+   ten nominal block thicknesses, a stand-in for the load the point carries;
+   m_bar/m of A and B (0 if static); body inertia diagonals over m_bar
+   L_bar^2 (0 if static); mu; matched previous-frame impulses over m_bar |g|
+   h; matched flag; ground flag. */
 #define FEAT_MASS 0.015
 #define FEAT_LEN 0.075
+#define FEAT_COLUMN 0.15
 static void features(or_episode* E, const or_params* P, double h) {
   double gh = norm3(P->gravity) * h;
   double sI = 1.0 / (FEAT_MASS * FEAT_LEN * FEAT_LEN);
+  double ztop = 0.0;
+  for (int i = 0; i < E->nb; ++i) {
+    const or_body* B = &E->b[i];
+    if (!B->active || B->is_static) continue;
+    double ez = fabs(B->R[2][0]) * B->half[0] + fabs(B->R[2][1]) * B->half[1] + fabs(B->R[2][2]) * B->half[2];
+    if (B->x[2] + ez > ztop) ztop = B->x[2] + ez;
+  }
   for (int c = 0; c < E->np; ++c) {
     or_pair* pr = &E->pairs[c];
     or_body *A = body_ref(E, pr->a), *B = body_ref(E, pr->b);
@@ -944,7 +956,9 @@ static void features(or_episode* E, const or_params* P, double h) {
       double* f = pr->feat[i];
       f[0] = dot3(u, pr->n) / gh; f[1] = dot3(u, pr->t1) / gh; f[2] = dot3(u, pr->t2) / gh;
       f[3] = P->contact_margin > 0 ? pr->depth[i] / P->contact_margin : 0.0;
-      for (int k = 0; k < 3; ++k) { f[4 + k] = pr->n[k]; f[7 + k] = pr->t1[k]; }
+      for (int k = 0; k < 3; ++k) f[4 + k] = pr->n[k];
+      f[7] = pr->t1[0]; f[8] = pr->t1[1];
+      f[9] = (ztop - pr->p[i][2]) / FEAT_COLUMN;
       f[10] = FEAT_MASS * A->invm; f[11] = FEAT_MASS * B->invm;
       for (int k = 0; k < 3; ++k) { f[12 + k] = IA[k]; f[15 + k] = IB[k]; }
       f[18] = pr->mu;

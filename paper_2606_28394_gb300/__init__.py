@@ -128,6 +128,7 @@ _sig = {
     "jb_mlp_save": (C.c_int32, [_vp, _fp, _vp]),
     "jb_mlp_forward": (C.c_int32, [_vp, _vp, C.c_int32, _vp, _vp, C.c_size_t, _vp]),
     "jb_mlp_grad": (C.c_int32, [_vp, _vp, _vp, C.c_int32, _vp, _vp, _vp, C.c_size_t, _vp]),
+    "jb_mlp_scratch_error": (C.c_int32, [_vp, C.c_size_t, _vp, C.POINTER(C.c_int32)]),
     "jb_mlp_adamw": (C.c_int32, [_vp, _vp, C.c_int32, C.c_float, C.c_float, C.c_float, C.c_float,
                                  C.c_float, _vp]),
     "jb_mlp_train_step": (C.c_int32, [_vp, _vp, _vp, C.c_int32, C.c_int32, C.c_float, C.c_float,

@@ -8,7 +8,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libjb.so")
-SOURCES = ["jb_kernels.cu", "jb_capi.cu", "jb_mlp.cu", "jb_peak.cu"]
+SOURCES = ["jb_kernels.cu", "jb_capi.cu", "jb_mlp.cu", "jb_mlp_tc.cu", "jb_peak.cu"]
 HEADERS = ["jb_internal.cuh", "jb_mlp.cuh", os.path.join("..", "..", "include", "jb.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -98,6 +98,9 @@ constexpr int kRecFloats = 27;   // recorder row: features, then converged impul
 // normalisation scales of the features (nominal block mass and length)
 constexpr float kFeatMass = 0.015f;
 constexpr float kFeatLen = 0.075f;
+// load-above feature: column height above a contact point in units of ten
+// nominal block thicknesses (0.15 m)
+constexpr float kFeatColumnInv = 1.f / 0.15f;
 
 struct Dev {
   int E, B, nb_max, pc_max;

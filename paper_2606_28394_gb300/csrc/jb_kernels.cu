@@ -1326,6 +1326,15 @@ __device__ StepOut substep(const Dev& D, const Ep& E, EpState& st, float h) {
   const float imp_scale = kFeatMass * gh;   // impulse unit m_bar g h
   const float inv_imp = 1.f / imp_scale;
   const float inv_mc = Pm.contact_margin > 0.f ? 1.f / Pm.contact_margin : 0.f;
+  // top of the episode's column of blocks: the highest AABB top of its active
+  // dynamic bodies (load-above feature)
+  float ztop = 0.f;
+  if (want_features) {
+    float zt = 0.f;
+    for (int i = lane; i < E.nb; i += 32)
+      if ((s.flags[i] & kActive) && !(s.flags[i] & kStatic)) zt = fmaxf(zt, s.at(FX + 2, i) + s.at(FE + 2, i));
+    ztop = warp_max(zt);
+  }
   for (int p = lane; p < npairs; p += 32) {
     uint32_t key = Bc.key[p];
     int a = (int)(key >> 16) - 1, b = (int)(key & 0xffff);
@@ -1397,13 +1406,15 @@ __device__ StepOut substep(const Dev& D, const Ep& E, EpState& st, float h) {
       W(10, q[7]); W(11, q[8]); W(12, q[9]);
       if (want_features && (all_features || q[10] == 0.f)) {
         // warm-start features: pre-solve relative velocity in the contact
-        // frame, depth, frame, inverse masses, body inertias, mu, previous
-        // impulses and two flags, normalised by the nominal block
+        // frame, depth, frame (n, t1.x, t1.y; t1.z follows from n), the
+        // height of the column above the point, inverse masses, body
+        // inertias, mu, previous impulses and two flags, normalised by the
+        // nominal block
         const float3 u = (s.ld3(FV, b) + cross(s.ld3(FW, b), rB)) - (s.ld3(FV, ia) + cross(s.ld3(FW, ia), rA));
         float* f = Bc.x + ((size_t)p * kMaxPts + k) * kFeatures;
         f[0] = dot(u, n) * inv_gh; f[1] = dot(u, t1) * inv_gh; f[2] = dot(u, t2) * inv_gh;
         f[3] = dep * inv_mc;
-        f[4] = n.x; f[5] = n.y; f[6] = n.z; f[7] = t1.x; f[8] = t1.y; f[9] = t1.z;
+        f[4] = n.x; f[5] = n.y; f[6] = n.z; f[7] = t1.x; f[8] = t1.y; f[9] = (ztop - pp.z) * kFeatColumnInv;
         f[10] = kFeatMass * ima; f[11] = kFeatMass * imb;
         f[12] = Ibody_a.x; f[13] = Ibody_a.y; f[14] = Ibody_a.z;
         f[15] = Ibody_b.x; f[16] = Ibody_b.y; f[17] = Ibody_b.z;

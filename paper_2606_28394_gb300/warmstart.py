@@ -15,9 +15,9 @@ import math
 
 import numpy as np
 
-from . import (Batch, check, jb_mlp_bytes, jb_mlp_forward, jb_mlp_grad, jb_mlp_load, jb_mlp_param_count,
-               jb_mlp_save, jb_mlp_scratch_bytes, jb_mlp_train_step, jb_set_recorder, jb_set_recorder_points,
-               jb_set_warmstart_mlp,
+from . import (JB_ECUDA, Batch, JBError, check, jb_mlp_bytes, jb_mlp_forward, jb_mlp_grad, jb_mlp_load, jb_mlp_param_count,
+               jb_mlp_save, jb_mlp_scratch_bytes, jb_mlp_scratch_error, jb_mlp_train_step, jb_set_recorder,
+               jb_set_recorder_points, jb_set_warmstart_mlp,
                _fp)
 
 N_IN, N_HID, N_OUT = 24, 128, 3
@@ -68,6 +68,17 @@ class Network:
             self._scratch = self.torch.empty(need, dtype=self.torch.uint8, device=self.device)
         return self._scratch
 
+    def check_kernel(self):
+        """Raises if the last tensor-core launch on this scratch gave up
+        waiting for its matrix products (its outputs are then not valid)."""
+        if self._scratch is None:
+            return
+        flag = C.c_int32(0)
+        check(jb_mlp_scratch_error(self._scratch.data_ptr(), self._scratch.numel(), self.stream, C.byref(flag)),
+              "jb_mlp_scratch_error")
+        if flag.value:
+            raise JBError(JB_ECUDA, "warm-start network kernel: a tensor-core wait ran out")
+
     def forward(self, x):
         """x: float32 device tensor [n, 24] -> [n, 3]."""
         x = x.contiguous()
@@ -76,6 +87,7 @@ class Network:
         sc = self.scratch(n)
         check(jb_mlp_forward(self.block.data_ptr(), x.data_ptr(), n, y.data_ptr(), sc.data_ptr(), sc.numel(),
                              self.stream), "jb_mlp_forward")
+        self.check_kernel()
         return y
 
     def grad(self, x, t):
@@ -147,6 +159,7 @@ def train(rows, epochs=30, batch=8192, lr=3e-4, wd=1e-4, val_frac=0.2, seed=0, d
             cur = lr / 20 + 0.5 * (lr - lr / 20) * (1 + math.cos(math.pi * it / total))
             net.train_step(x_tr[lo:hi], t_tr[lo:hi], cur, wd)
             it += 1
+        net.check_kernel()
         tl = float(net.grad(x_tr[: min(len(x_tr), 65536)], t_tr[: min(len(x_tr), 65536)])[1].item())
         vl = float(net.grad(x_va, t_va)[1].item()) if len(x_va) else float("nan")
         hist.append((ep, tl, vl))

@@ -84,7 +84,8 @@ def test_recorder_features_of_a_resting_block():
     for r in rows[:4]:        # first step: nothing to match yet
         assert np.allclose(r[0:3], [-1, 0, 0], atol=1e-12)        # u = -g h along n
         assert abs(r[3]) < 1e-9                                   # touching
-        assert np.allclose(r[4:10], [0, 0, 1, 1, 0, 0])
+        assert np.allclose(r[4:9], [0, 0, 1, 1, 0])
+        assert abs(r[9] - 2 * hz / 0.15) < 1e-9                   # column of one block above z = 0
         assert r[10] == 0 and abs(r[11] - 0.015 / m) < 1e-12
         assert np.allclose(r[12:15], 0) and np.allclose(r[15:18], I)
         assert abs(r[18] - mu) < 1e-7 and np.allclose(r[19:23], 0) and r[23] == 1
@@ -129,9 +130,10 @@ def test_recorder_features_of_a_moving_spinning_pair():
     """The A28 features of a block-on-block pair in the air, both moving and
     spinning, masses 2:1: per point, the relative velocity
     (v_B + w_B x r_B) - (v_A + w_A x r_A) after the gravity predictor, in
-    the contact frame, over g h; then depth / margin, n, t1, the scaled
-    inverse masses and inertias of A and B in that order, mu, zero
-    impulses, and the unmatched and not-ground flags."""
+    the contact frame, over g h; then depth / margin, n, t1.x, t1.y, the
+    column height above the point over 0.15 m, the scaled inverse masses
+    and inertias of A and B in that order, mu, zero impulses, and the
+    unmatched and not-ground flags."""
     hx, hy, hz = 0.0375, 0.0125, 0.0075
     mA, mB, mu, pen = 0.030, 0.015, 0.4, 1e-4
     vA, wA = np.array([0.1, -0.05, 0.02]), np.array([0.5, -0.3, 0.8])
@@ -164,7 +166,11 @@ def test_recorder_features_of_a_moving_spinning_pair():
         u = (vB + g + np.cross(wB, p - xB)) - (vA + g + np.cross(wA, p - xA))
         assert np.allclose(r[0:3] * gh, [u @ n, u @ t1, u @ t2], atol=1e-13)
         assert abs(r[3] - d / prm["contact_margin"]) < 1e-12
-        assert np.allclose(r[4:7], n) and np.allclose(r[7:10], t1)
+        assert np.allclose(r[4:7], n) and np.allclose(r[7:9], t1[:2])
+        # the column above the interface: B's top (1 + 3 hz - pen) minus the
+        # point, halfway into the overlap (1 + hz - pen / 2)
+        assert abs(p[2] - (1.0 + hz - pen / 2)) < 1e-12
+        assert abs(r[9] - (2 * hz - pen / 2) / 0.15) < 1e-10
         assert abs(r[10] - 0.015 / mA) < 1e-12 and abs(r[11] - 0.015 / mB) < 1e-12
         assert np.allclose(r[12:15], I_box(mA) * scale_I, rtol=1e-12)
         assert np.allclose(r[15:18], I_box(mB) * scale_I, rtol=1e-12)
