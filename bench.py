@@ -148,12 +148,17 @@ def reduce_ranks(times_ms, walls_s, body_steps, device, dist=None):
 
 MLP_FLOP = 2.0 * (24 * 128 + 128 * 128 + 128 * 3)   # per predicted contact point
 
-# DRAM bytes (read + write) of one full-job episode_kernel launch, from
+# DRAM bytes (read + write) of episode_kernel per body-step, from one ncu
+# capture of a small case of the same workload (counters stay off the full
+# job), scaled to a launch by its body-steps: the traffic is the per-step
+# contact records and warm-start caches of each episode plus the initial state
+# load, so it grows with the episode-steps run.  Captured with
 # `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none
-#  -k regex:episode_kernel -s 3 -c 1 python bench.py --warm-start plain --no-cpu --no-compare`
-# (1 pass): 13.01 MB read + 493.83 MB written.  Valid only for the kernel
-# sources it was taken on; any change to them reports null.
-TRAFFIC = {"bytes": 13009152.0 + 493827584.0, "workload": "friction", "sources_sha1": "f6bf30d931e87c346900c53fcb010d71c4773b7b"}
+#  -k regex:episode_kernel -s 3 -c 1 python bench.py --warm-start plain --no-cpu --no-compare
+#  --episodes 45 --max-steps 300 --steps 1 --warmup 3` (1 pass).  Valid only for
+# the kernel sources it was taken on; any change to them reports null.
+TRAFFIC = {"bytes_per_body_step": None, "case": "45 episodes x 300 steps", "workload": "friction",
+           "sources_sha1": None}
 
 
 def kernel_sources_sha1():
@@ -184,28 +189,29 @@ def prepare_learned(args, rank, prm, device):
     t2 = time.perf_counter()
     sc2, pr2, _ = make_workload(args.workload, 4001 + rank)
     s_ev, p_ev = synth.subset(sc2, pr2, np.linspace(0, sc2.n_episodes - 1, args.gate_episodes).round().astype(int))
-    gate = ws.evaluate(s_ev, p_ev, prm, net, mode=2, max_steps=args.gate_steps, device=device)
+    # the gate: both warm starts from identical states along plain PGS's
+    # trajectory (the network's own effect, free of trajectory divergence)
+    gate = ws.paired(s_ev, p_ev, prm, net, steps=args.gate_steps, mode=2, device=device)
+    # whole trajectories of both arms on the same episodes (context)
+    traj = ws.evaluate(s_ev, p_ev, prm, net, mode=2, max_steps=args.gate_steps, device=device)
     s_cold, _ = synth.subset(sc2, pr2, np.linspace(0, sc2.n_episodes - 1, 10).round().astype(int))
     cold = ws.cold_start_gain(s_cold, prm, net, steps=12, device=device)
-    # short episodes (the first 24 steps of the gate towers, from their cold
-    # start): where contacts without a previous impulse carry much of the work
-    short = ws.evaluate(s_ev, p_ev, prm, net, mode=2, max_steps=24, device=device)
     t3 = time.perf_counter()
     info = {"samples": int(rows.shape[0]), "collect_s": t1 - t0, "train_s": t2 - t1, "gate_s": t3 - t2,
             "epochs": 30, "final_train_loss": hist[-1][1], "final_val_loss": hist[-1][2],
             "cold_contacts": {"episodes": 10, "steps": 12, "plain_sweeps_per_solve": cold[0],
                               "learned_sweeps_per_solve": cold[1], "gain": cold[2]},
-            "short_episodes": {"episodes": args.gate_episodes, "steps": 24,
-                               "plain_body_steps_per_s": short["plain"]["body_steps_per_s"],
-                               "learned_body_steps_per_s": short["learned"]["body_steps_per_s"],
-                               "plain_sweeps_per_solve": short["plain"]["sweeps_per_solve"],
-                               "learned_sweeps_per_solve": short["learned"]["sweeps_per_solve"],
-                               "learned_over_plain": short["learned"]["body_steps_per_s"]
-                               / max(short["plain"]["body_steps_per_s"], 1e-12)},
             "gate": {"episodes": args.gate_episodes, "steps": args.gate_steps,
-                     "plain_sweeps_per_solve": gate["plain"]["sweeps_per_solve"],
-                     "learned_sweeps_per_solve": gate["learned"]["sweeps_per_solve"],
-                     "gain": gate["gain"]}, "kept": bool(gate["keep"])}
+                     "kind": "paired: both warm starts solve every step from the same snapshot along plain "
+                             "PGS's trajectory",
+                     "plain_sweeps": float(gate["plain"].sum()), "learned_sweeps": float(gate["learned"].sum()),
+                     "first_step_gain": float(gate["plain"][0] / max(gate["learned"][0], 1.0)),
+                     "gain": gate["gain"], "learned_capped": gate["learned_capped"]},
+            "trajectories": {"episodes": args.gate_episodes, "steps": args.gate_steps,
+                             "plain_sweeps_per_solve": traj["plain"]["sweeps_per_solve"],
+                             "learned_sweeps_per_solve": traj["learned"]["sweeps_per_solve"],
+                             "gain": traj["gain"]},
+            "kept": bool(gate["gain"] > 1.0)}
     return net, info
 
 
@@ -636,9 +642,11 @@ def main():
     achieved = flops / (ms / args.steps / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
             "frac": achieved / peak_tf,
-            "traffic": (TRAFFIC["bytes"] if (TRAFFIC["sources_sha1"] == kernel_sources_sha1()
-                                             and args.workload == TRAFFIC["workload"] and not args.episodes
-                                             and not args.fixed_iters) else None),
+            "traffic": (TRAFFIC["bytes_per_body_step"] * body_steps
+                        if (TRAFFIC["bytes_per_body_step"] and TRAFFIC["sources_sha1"] == kernel_sources_sha1()
+                            and args.workload == TRAFFIC["workload"] and not args.fixed_iters) else None),
+            "traffic_note": f"ncu DRAM bytes per body-step on {TRAFFIC['case']} of this workload x the launch's "
+                            f"body-steps",
             "mlp_flops_per_launch": mlp_flops,
             "mlp_roofline_ms": mlp_flops / (float(peaks.get("bf16_tflops", 1892.9)) * 1e12) * 1e3,
             "peak_note": (f"measured FP32 multiply-add rate of this GPU (jb_fma_probe, {peak['sms']} SMs from the "
@@ -663,7 +671,7 @@ def main():
                        "l2": "flushed (256 MB write) before every timed step",
                        "warmup": f"{args.warmup} passes of the job truncated to {args.warmup_steps} physics steps",
                        "episodes": scene.n_episodes, "bodies": scene.n_bodies},
-            "warm_start": {"mode": "learned (network on unmatched points, previous-frame elsewhere)"
+            "warm_start": {"mode": "learned (network on the points of new pairs, previous-frame elsewhere)"
                            if kept else "plain (previous-frame)"
                            + (": the gate rejected the network" if learned else ""),
                            "training": learned, "comparison": compare,

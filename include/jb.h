@@ -88,8 +88,10 @@ typedef struct {
   float aabb_eps;           /* Eq. aabb epsilon, m */
   float gravity[3];         /* m/s^2 */
   int32_t warm_start;       /* 0 none, 1 previous-frame impulses, 2 previous-frame where a
-                               point matches and the warm-start network elsewhere, 3 the
-                               network for every point (2 and 3 need jb_set_warmstart_mlp) */
+                               point matches, the warm-start network for the points of new
+                               pairs (no point matched) and zero for the unmatched points of
+                               other pairs, 3 the network for every point (2 and 3 need
+                               jb_set_warmstart_mlp) */
   float match_radius;       /* warm-start point match radius, m */
   float fall_frac;          /* Eq. collapse f_d */
   float collapse_ek;        /* Eq. collapse eps_k, J */
@@ -388,9 +390,10 @@ jb_status jb_set_warmstart_mlp(jb_batch* b, const void* d_mlp);
 jb_status jb_set_recorder(jb_batch* b, float* d_rows, int32_t capacity, int32_t* d_count, int32_t every);
 
 /* Which points the recorder takes: 0 (the default) every point of a recorded
- * solve; 1 only the points without a previous-frame impulse, the ones the
- * learned warm start predicts in mode 2 (so that the training set has the
- * distribution the network meets).  JB_EINVAL for other values. */
+ * solve; 1 only the points of pairs none of whose points had a previous-frame
+ * impulse, the ones the learned warm start predicts in mode 2 (so that the
+ * training set has the distribution the network meets).  JB_EINVAL for other
+ * values. */
 jb_status jb_set_recorder_points(jb_batch* b, int32_t unmatched_only);
 
 size_t jb_mlp_bytes(void);              /* device bytes of a network block */

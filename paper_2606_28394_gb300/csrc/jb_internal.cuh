@@ -126,7 +126,7 @@ struct Dev {
   float* rec;
   int32_t* rec_count;
   int rec_cap, rec_every;
-  int rec_unmatched;      // 1: the recorder takes only points without a previous-frame impulse
+  int rec_unmatched;      // 1: the recorder takes only the points of pairs with no previous-frame impulse
 };
 
 // Error reporting shared by the library's translation units.

@@ -948,7 +948,8 @@ __device__ __forceinline__ void accel_step(const SolverRef& r, float* acc, const
 #undef VF
 
 // ----------------------------------------------------- learned warm start
-// The warp collects the points to predict (ids p * 4 + k) into the
+// The warp collects the points to predict (ids p * 4 + k: every point in
+// mode 3, the points of new pairs in mode 2) into the
 // candidate array (free after the colouring), runs the network on tiles of 16
 // rows on the tensor cores and writes the projected impulses (lambda_n >= 0,
 // |lambda_t| <= mu lambda_n) as the points' starting impulses.
@@ -972,8 +973,13 @@ __device__ __noinline__ int mlp_warm_start(const Dev& D, const Ep& E, const BufV
     if (p < npairs) {
       int np = Bc.feat[p] >> 24;
       const float* pt = Bc.pt + (size_t)p * kMaxPts * kNatPtFloats;
+      // mode 2: the points of pairs none of whose points inherited an impulse
+      // (new pairs); a point that appears in a pair that already carries
+      // impulses starts at zero, as in plain PGS
+      bool any_matched = false;
+      for (int k = 0; k < np; ++k) any_matched |= pt[k * kNatPtFloats + 10] != 0.f;
       for (int k = 0; k < np; ++k)
-        if (all_points || pt[k * kNatPtFloats + 10] == 0.f) ids[mine++] = (uint32_t)(p * kMaxPts + k);
+        if (all_points || !any_matched) ids[mine++] = (uint32_t)(p * kMaxPts + k);
     }
     int incl = mine;
 #pragma unroll
@@ -1533,8 +1539,10 @@ __device__ StepOut substep(const Dev& D, const Ep& E, EpState& st, float h) {
     for (int p = lane; p < npairs; p += 32) {
       int np = Bc.feat[p] >> 24;
       const float* pt = Bc.pt + (size_t)p * kMaxPts * kNatPtFloats;
+      bool any_matched = false;
+      for (int k = 0; k < np; ++k) any_matched |= pt[k * kNatPtFloats + 10] != 0.f;
+      if (D.rec_unmatched && any_matched) continue;
       for (int k = 0; k < np; ++k) {
-        if (D.rec_unmatched && pt[k * kNatPtFloats + 10] != 0.f) continue;
         int slot = atomicAdd(D.rec_count, 1);
         if (slot >= D.rec_cap) break;
         float* row = D.rec + (size_t)slot * kRecFloats;

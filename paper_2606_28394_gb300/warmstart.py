@@ -115,7 +115,7 @@ def collect(scene, prot, params, capacity, every=1, max_steps=1 << 30, device="c
     """Runs the plain solver through the schedule with the recorder on; returns
     the recorded rows [n, 27] (device tensor): features, then the converged
     impulses in units of m_bar |g| h.  unmatched_only records only the points
-    without a previous-frame impulse (the points mode 2 predicts)."""
+    of pairs with no previous-frame impulse (the points mode 2 predicts)."""
     import torch
     prm = dict(params, warm_start=1)
     b = Batch(scene, prm, max_moves=int(prot.off[-1]), device=device)
@@ -170,7 +170,7 @@ def train(rows, epochs=30, batch=8192, lr=3e-4, wd=1e-4, val_frac=0.2, seed=0, d
 
 def evaluate(scene, prot, params, net, mode=2, max_steps=1 << 30, device="cuda"):
     """Sweeps per solve and body-steps of the plain solver and of the learned
-    warm start (mode 2: unmatched points; 3: all points) on the same episodes,
+    warm start (mode 2: points of new pairs; 3: all points) on the same episodes,
     and whether the gate keeps the network."""
     import torch
     out = {}
@@ -211,3 +211,41 @@ def cold_start_gain(scene, params, net, steps=20, mode=2, device="cuda"):
         st = b.stats()
         out[name] = float(st["total_sweeps"].sum() / max(st["solves"].sum(), 1))
     return out["plain"], out["learned"], out["plain"] / max(out["learned"], 1e-9)
+
+
+def paired(scene, prot, params, net, steps, mode=2, device="cuda"):
+    """Sweeps of both warm starts from identical states.  Along plain PGS's
+    own trajectory every step is solved twice from the same snapshot (the
+    bodies, the schedule position and the previous-frame impulse cache):
+    once with the network's starts, once with plain PGS's zero starts at the
+    points without a previous impulse; the plain solve carries the trajectory
+    on.  Whole trajectories of the two arms part after the first solve (the
+    impulses over a stack's redundant supports are not unique, and the
+    episodes are chaotic), so comparing them measures where each trajectory
+    went as much as what the network saves; this pairing measures only the
+    latter.  Returns the per-step sweep sums of both arms and their totals'
+    ratio (plain / learned)."""
+    b = Batch(scene, dict(params, warm_start=1), max_moves=int(prot.off[-1]), device=device)
+    check(jb_set_warmstart_mlp(b.h, net.block.data_ptr()), "jb_set_warmstart_mlp")
+    b.set_protocol(prot)
+    plain, learned = [], []
+    capped = 0
+    total = lambda: float(b.stats()["total_sweeps"].sum())
+    for _ in range(steps):
+        snap = b.save_state()
+        st0 = b.stats()
+        s0, c0 = float(st0["total_sweeps"].sum()), int(st0["capped_solves"].sum())
+        b.set_params(dict(params, warm_start=mode))
+        b.run_protocol(1)
+        st = b.stats()
+        learned.append(float(st["total_sweeps"].sum()) - s0)
+        capped += int(st["capped_solves"].sum()) - c0
+        b.load_state(snap)
+        s0 = total()
+        b.set_params(dict(params, warm_start=1))
+        b.run_protocol(1)
+        plain.append(total() - s0)
+    plain, learned = np.array(plain), np.array(learned)
+    st = b.stats()
+    return {"plain": plain, "learned": learned, "gain": float(plain.sum() / max(learned.sum(), 1.0)),
+            "plain_capped": int(st["capped_solves"].sum()), "learned_capped": capped}
