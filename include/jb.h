@@ -88,9 +88,10 @@ typedef struct {
   float aabb_eps;           /* Eq. aabb epsilon, m */
   float gravity[3];         /* m/s^2 */
   int32_t warm_start;       /* 0 none, 1 previous-frame impulses, 2 previous-frame where a
-                               point matches, the warm-start network for the points of new
-                               pairs (no point matched) and zero for the unmatched points of
-                               other pairs, 3 the network for every point (2 and 3 need
+                               point matches; on a step where at least half of the
+                               episode's pairs are new (no point matched), the warm-start
+                               network for the points of the new pairs; zero elsewhere;
+                               3 the network for every point (2 and 3 need
                                jb_set_warmstart_mlp) */
   float match_radius;       /* warm-start point match radius, m */
   float fall_frac;          /* Eq. collapse f_d */

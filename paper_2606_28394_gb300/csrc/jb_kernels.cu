@@ -949,7 +949,8 @@ __device__ __forceinline__ void accel_step(const SolverRef& r, float* acc, const
 
 // ----------------------------------------------------- learned warm start
 // The warp collects the points to predict (ids p * 4 + k: every point in
-// mode 3, the points of new pairs in mode 2) into the
+// mode 3; in mode 2 the points of new pairs, on steps where at least half of
+// the pairs are new) into the
 // candidate array (free after the colouring), runs the network on tiles of 16
 // rows on the tensor cores and writes the projected impulses (lambda_n >= 0,
 // |lambda_t| <= mu lambda_n) as the points' starting impulses.
@@ -966,6 +967,23 @@ __device__ __noinline__ int mlp_warm_start(const Dev& D, const Ep& E, const BufV
   const int lcap = ccap - 64;
   const int g = lane >> 2, t = lane & 3;
   int cnt = 0, predicted = 0;
+  if (!all_points) {
+    // mode 2 predicts only on a step where at least half of the episode's
+    // pairs are new (an episode's first step, a large rearrangement): there
+    // the network's starts are reliably closer to the converged impulses
+    // than zero; a few pairs forming beside many settled ones start at zero
+    int nnew = 0;
+    for (int p = lane; p < npairs; p += 32) {
+      const int np = Bc.feat[p] >> 24;
+      const float* pt = Bc.pt + (size_t)p * kMaxPts * kNatPtFloats;
+      bool matched = false;
+      for (int k = 0; k < np; ++k) matched |= pt[k * kNatPtFloats + 10] != 0.f;
+      nnew += matched ? 0 : 1;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nnew += __shfl_xor_sync(FULL, nnew, o);
+    if (2 * nnew < npairs) return 0;
+  }
   for (int p0 = 0; p0 < npairs; p0 += 32) {
     const int p = p0 + lane;
     int mine = 0;

@@ -1,5 +1,6 @@
-// Warm-start network: host entry points, fragment packing for the episode
-// kernel's in-warp inference, and AdamW on the FP32 master weights.  Batch
+// Warm-start network: host entry points, packing (the BF16 fragments of the
+// episode kernel's in-warp inference and the BF16 weight image of the
+// tensor-core kernel), and AdamW on the FP32 master weights.  Batch
 // inference and the training gradient run in the fused tcgen05 kernel of
 // jb_mlp_tc.cu.  The contact features and targets come from the episode
 // kernel's recorder.
@@ -47,9 +48,36 @@ __global__ void mlp_pack_kernel(unsigned char* mlp) {
   if (i < kW3TTiles * 32) { pack_tiles(pk + L.p3t, kOutPadK / 16, kHid / 8, w3t, i); return; }
   i -= kW3TTiles * 32;
   if (i < kW2TTiles * 32) { pack_tiles(pk + L.p2t, kHid / 16, kHid / 8, w2t, i); return; }
+  i -= kW2TTiles * 32;
+  // the tensor-core kernel's weight image, 8 BF16 (16 bytes) per thread
+  if (i < kImgBytes / 16) {
+    unsigned char* img = mlp + L.img;
+    int base, K;
+    auto src = [&](int r, int k) -> float {
+      switch (base) {
+        case kImgW1T: return w1(k, r);            // W1^T[j][f] = W1[f][j]
+        case kImgW2T: return W2[k * kHid + r];    // W2^T[o][i] = W2[i][o]
+        case kImgW2: return W2[r * kHid + k];
+        case kImgW3T: return w3(k, r);            // W3^T[o][k] = W3[k][o]
+        default: return w3(r, k);                 // W3[k][o]
+      }
+    };
+    int c = i;
+    // chunks per tile: [128][32] 512, [128][128] 2048 twice, [16][128] 256, [128][16] 256
+    if (c < 512) { base = kImgW1T; K = 32; }
+    else if ((c -= 512) < 2048) { base = kImgW2T; K = kHid; }
+    else if ((c -= 2048) < 2048) { base = kImgW2; K = kHid; }
+    else if ((c -= 2048) < 256) { base = kImgW3T; K = kHid; }
+    else { c -= 256; base = kImgW3; K = 16; }
+    const int r = c / (K / 8), k = (c % (K / 8)) * 8;
+    uint32_t w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) w[q] = pack_bf16x2(src(r, k + 2 * q), src(r, k + 2 * q + 1));
+    *reinterpret_cast<uint4*>(img + base + kmaj_off(r, k, K)) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
 }
 
-constexpr int kPackThreads = (kW1Tiles + kW2Tiles + kW3Tiles + kW3TTiles + kW2TTiles) * 32;
+constexpr int kPackThreads = (kW1Tiles + kW2Tiles + kW3Tiles + kW3TTiles + kW2TTiles) * 32 + kImgBytes / 16;
 
 // AdamW on the master weights (decoupled weight decay on the matrices only).
 __global__ void mlp_adamw_kernel(unsigned char* mlp, const float* __restrict__ grad, float lr, float b1, float b2,

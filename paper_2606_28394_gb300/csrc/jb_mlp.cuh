@@ -23,6 +23,21 @@ constexpr int kW3Tiles = (kHid / 16) * (kOutPad / 8);    // 8
 constexpr int kW3TTiles = (kOutPadK / 16) * (kHid / 8);  // 16
 constexpr int kW2TTiles = (kHid / 16) * (kHid / 8);      // 128
 
+// BF16 image of the weights in the shared-memory layout of the tensor-core
+// kernel (jb_mlp_tc.cu), written by the pack kernel after every parameter
+// change and copied to shared memory in one bulk transfer.  Tiles are
+// K-major without swizzle: element (r, k) of a [R][K] tile at byte
+// (r / 8) * K * 16 + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2.
+constexpr int kImgW1T = 0;                          // W1^T [128 hidden][32 features]
+constexpr int kImgW2T = kImgW1T + 128 * 32 * 2;     // W2^T [128 out][128 in]
+constexpr int kImgW2 = kImgW2T + 128 * 128 * 2;     // W2 [128 in][128 out]
+constexpr int kImgW3T = kImgW2 + 128 * 128 * 2;     // W3^T [16 outputs][128 hidden]
+constexpr int kImgW3 = kImgW3T + 16 * 128 * 2;      // W3 [128 hidden][16 outputs]
+constexpr int kImgBytes = kImgW3 + 128 * 16 * 2;    // 81,920
+__host__ __device__ inline uint32_t kmaj_off(int r, int k, int K) {
+  return (uint32_t)((r >> 3) * (K * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
 // Layout of the network block in device memory (FP32 unless noted).
 struct MlpLayout {
   // master weights, row-major [in][out]
@@ -33,6 +48,7 @@ struct MlpLayout {
   // packed BF16 B fragments (uint2 per lane per tile, 8 bytes)
   int p1, p2, p3, p3t, p2t;   // offsets in uint2 units from pack_base
   int pack_base;              // byte offset of the packed block
+  int img;                    // byte offset of the BF16 weight image (kImgBytes)
   int bytes;
 };
 
@@ -57,7 +73,8 @@ __host__ __device__ inline MlpLayout mlp_layout() {
   L.p3 = u; u += kW3Tiles * 32;
   L.p3t = u; u += kW3TTiles * 32;
   L.p2t = u; u += kW2TTiles * 32;
-  L.bytes = ((bytes + u * 8) + 255) & ~255;
+  L.img = ((bytes + u * 8) + 255) & ~255;
+  L.bytes = (L.img + kImgBytes + 255) & ~255;
   return L;
 }
 

@@ -25,6 +25,10 @@
 // the weight gradient over rows), so the epilogues write it twice: as the
 // thread's own row, and transposed as the thread's own column.
 //
+// The weights arrive in one bulk copy (cp.async.bulk, the TMA engine) of
+// the BF16 image that the pack kernel keeps in the network block in exactly
+// this layout; the rows are read by the threads (24 FP32 features each).
+//
 // Waits on the mbarrier are bounded (about one second); a wait that runs out
 // sets the error flag, and the CTA frees its TMEM and returns.
 #include <cuda_bf16.h>
@@ -63,11 +67,12 @@ constexpr int oR2 = oH1T + kSzH;        // H2 [rows][hidden]; then dH1^T [hidden
 constexpr int oR3 = oR2 + kSzH;         // H2^T [hidden][rows]; then dH2^T [hidden][rows]
 constexpr int kSmemBytes = oR3 + kSzH;  // 229,376
 static_assert(kSmemBytes <= 227 * 1024 - 2048, "fused tile must fit one CTA's shared memory");
+static_assert(oW1T == kImgW1T && oW2T == kImgW2T && oW2 == kImgW2 && oW3T == kImgW3T && oW3 == kImgW3 &&
+                  oXR == kImgBytes,
+              "the weight tiles are the pack kernel's image, byte for byte");
 
 // Byte offset of element (r, k) of a K-major tile with K columns.
-__device__ __forceinline__ uint32_t kmaj(int r, int k, int K) {
-  return (uint32_t)((r >> 3) * (K * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
-}
+__device__ __forceinline__ uint32_t kmaj(int r, int k, int K) { return kmaj_off(r, k, K); }
 
 // Shared-memory matrix descriptor: K-major, no swizzle, leading byte offset
 // 128 (the second core matrix of a K = 16 step), stride byte offset K * 16
@@ -146,20 +151,6 @@ __device__ __forceinline__ void st_bf16(unsigned char* sm, uint32_t off, float v
   *reinterpret_cast<__nv_bfloat16*>(sm + off) = __float2bfloat16_rn(v);
 }
 
-// One BF16 K-major tile [R][K] from an FP32 source src(r, k), 8 columns per
-// 16-byte store.
-template <class F>
-__device__ __forceinline__ void load_tile(unsigned char* sm, int off, int R, int K, int tid, F src) {
-  const int chunks = R * K / 8;
-  for (int c = tid; c < chunks; c += kRows) {
-    const int r = c / (K / 8), k = (c % (K / 8)) * 8;
-    uint32_t w[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) w[i] = pack_bf16x2(src(r, k + 2 * i), src(r, k + 2 * i + 1));
-    st16(sm, off + kmaj(r, k, K), w[0], w[1], w[2], w[3]);
-  }
-}
-
 // Epilogue of a [128 x 128] accumulator: value(c, v) of each column of this
 // thread's row, rounded to BF16, stored as row `tid` of the tile at `row_off`
 // (if >= 0) and as column `tid` of the tile at `col_off` (if >= 0); bit c of
@@ -230,19 +221,18 @@ __global__ void __launch_bounds__(kRows, 1)
                  "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  // weights as BF16 K-major tiles (padding zero)
-  const float* W1 = P + L.w1;
-  const float* W2 = P + L.w2;
-  const float* W3 = P + L.w3;
-  load_tile(sm, oW1T, kHid, 32, tid, [&](int j, int f) { return f < kFeat ? W1[f * kHid + j] : 0.f; });
-  load_tile(sm, oW2T, kHid, kHid, tid, [&](int k, int j) { return W2[j * kHid + k]; });
-  load_tile(sm, oW3T, 16, kHid, tid, [&](int o, int k) { return o < kOut ? W3[k * kOut + o] : 0.f; });
-  if (mode == 1) {
-    load_tile(sm, oW2, kHid, kHid, tid, [&](int j, int k) { return W2[j * kHid + k]; });
-    load_tile(sm, oW3, kHid, 16, tid, [&](int k, int o) { return o < kOut ? W3[k * kOut + o] : 0.f; });
+  // the weights: one bulk copy (TMA) of the BF16 image the pack kernel keeps
+  // in the block, in exactly this shared-memory layout
+  if (tid == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(kImgBytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(sm + oW1T)),
+                 "l"(mlp + L.img), "r"(kImgBytes), "r"(mb)
+                 : "memory");
+  }
+  if (mode == 1)
     // X^T rows of the padding features stay zero
     for (int f = kFeat; f < 32; ++f) st_bf16(sm, oXT + kmaj(f, tid, 128), 0.f);
-  }
   fence_async_smem();
   tc_before_sync();
   __syncthreads();
@@ -251,6 +241,9 @@ __global__ void __launch_bounds__(kRows, 1)
   const uint32_t tl = tb + ((uint32_t)(warp * 32) << 16);   // this warp's TMEM lanes
   const uint32_t s0 = smem_u32(sm);
   uint32_t phase = 0;
+  if (!mbar_wait(mb, phase)) bad = 1;   // the weight image
+  phase ^= 1u;
+  __syncthreads();
 
   // the issuing thread orders its MMAs after the epilogue's stores and TMEM
   // reads; every thread then waits for their completion
@@ -268,7 +261,7 @@ __global__ void __launch_bounds__(kRows, 1)
   };
 
   bool first = true;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, first = false) {
+  for (int tile = bad ? ntiles : (int)blockIdx.x; tile < ntiles; tile += gridDim.x, first = false) {
     const int row = tile * kRows + tid;
     const bool live = row < n;
     // X row -> X [rows][32] (A of D1) and, for the gradient, X^T [32][rows]

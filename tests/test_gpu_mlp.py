@@ -158,6 +158,55 @@ def test_learned_warm_start_converges_to_the_same_state(cuda_device, mode):
     assert np.abs(v - vo).max() < 1e-4 and (np.abs(w - wo).max(0) * diag).max() < 1e-4
 
 
+@pytest.mark.parametrize("n", [1, 127, 300, 20000])
+def test_tensor_core_kernel_matches_a_bf16_faithful_reference(cuda_device, n):
+    """The fused tcgen05 kernel against a PyTorch FP32 computation of the
+    same network with the kernel's BF16 roundings (inputs, weights, hidden
+    activations, the scaled output error and the backward activations) and
+    FP32 sums.  Only the summation order differs, but an activation that
+    lands near a BF16 rounding boundary can round the other way (2^-8
+    relative), so the forward agrees to 1e-3 relative and every gradient
+    block to 1e-2 relative of its largest entry with cosine above 0.9999.
+    n = 1 and 127 are one partial tile, 300 a ragged third tile, and 20000
+    rows are 157 tiles, more than one per SM, so CTAs accumulate the weight
+    sums in tensor memory across tiles."""
+    import torch
+    torch.manual_seed(n)
+    net = ws().Network(device="cuda:0", seed=3)
+    p = torch.from_numpy(net.params()).to("cuda:0")
+    sizes = [(24, 128), (128,), (128, 128), (128,), (128, 3), (3,)]
+    parts, o = [], 0
+    for sh in sizes:
+        k = int(np.prod(sh))
+        parts.append(p[o:o + k].view(*sh))
+        o += k
+    W1, b1, W2, b2, W3, b3 = parts
+    bf = lambda t: t.to(torch.bfloat16).float()
+    x = torch.randn(n, 24, device="cuda:0")
+    t = 0.1 * torch.randn(n, 3, device="cuda:0")
+    h1 = bf(torch.relu(bf(x) @ bf(W1) + b1))
+    h2 = bf(torch.relu(h1 @ bf(W2) + b2))
+    y_ref = h2 @ bf(W3) + b3
+    y = net.forward(x)
+    assert float((y - y_ref).abs().max()) <= 1e-3 * float(y_ref.abs().max())
+    g, loss = net.grad(x, t)
+    net.check_kernel()
+    e = y_ref - t
+    assert abs(float(loss) - float((e * e).sum()) / n) <= 1e-4 * float((e * e).sum()) / n
+    dy = bf(2.0 / n * e)
+    dh2 = bf((dy @ bf(W3).T) * (h2 > 0))
+    dh1 = bf((dh2 @ bf(W2).T) * (h1 > 0))
+    ref = [bf(x).T @ dh1, dh1.sum(0), h1.T @ dh2, dh2.sum(0), h2.T @ dy, dy.sum(0)]
+    o = 0
+    for r in ref:
+        k = r.numel()
+        got = g[o:o + k].view_as(r)
+        o += k
+        assert float((got - r).abs().max()) <= 1e-2 * float(r.abs().max()) + 1e-12
+        cos = torch.nn.functional.cosine_similarity(got.flatten(), r.flatten(), dim=0)
+        assert float(cos) > 0.9999
+
+
 def test_learned_warm_start_without_network_is_refused(cuda_device):
     scene = synth.build_scene([synth.Tower(levels=2)], 0)
     b = jb().Batch(scene, synth.params(warm_start=2))
