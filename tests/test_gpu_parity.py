@@ -544,7 +544,7 @@ def test_newton_restitution_fp32_and_parity(cuda_device):
 
 
 @pytest.mark.parametrize("accel,key", [(0, 0), (4, 0), (0, 1)])
-@pytest.mark.parametrize("name", ["tower18", "tower4_perturbed"])
+@pytest.mark.parametrize("name", ["tower18", "tower4_perturbed", "tower30"])
 def test_fixed_sweeps_match_the_oracle_in_colour_order(cuda_device, name, accel, key):
     """With the oracle sweeping in the library's colour order, the iterates
     themselves agree, not only the fixed point: one step of 20 fixed sweeps
@@ -552,9 +552,13 @@ def test_fixed_sweeps_match_the_oracle_in_colour_order(cuda_device, name, accel,
     checks the sweep arithmetic (the point-block rows, the packed impulse
     application, the colour schedule) row for row, and with accel = 4 the
     five conjugate-gradient steps in between (direction, beta, restart,
-    projection, impulse application); with key = 1 the height-bin colouring."""
+    projection, impulse application); with key = 1 the height-bin colouring.
+    A 30-level tower's colours hold 28-46 pairs, so there lanes also sweep
+    two pairs of a colour in one pass."""
     if name == "tower18":
         scene = synth.build_scene([synth.Tower()], 0)
+    elif name == "tower30":
+        scene = synth.build_scene([synth.Tower(levels=30)], 0)
     else:
         scene = synth.perturbed(synth.build_scene([synth.Tower(levels=4, mu=0.5)], 1), 5, dx=2e-4, dang=0.01)
     prm = synth.params(pgs_iters=20, pgs_accel_period=accel)
