@@ -211,3 +211,35 @@ def test_warm_start_match_follows_body_a():
     second = W.recorded()[4:8]
     assert np.all(second[:, 22] == 1)
     assert abs(second[:, 19].sum() - 1.0) < 1e-6   # the previous total normal impulse m g h
+
+
+def test_column_height_feature_of_a_block_on_its_edge():
+    """Feature 9 (the column height above a contact point over 0.15 m) of a
+    block resting on one long edge, turned 30 degrees about its length axis
+    and 20 degrees about z: the top of the column is the block's centre
+    height plus its rotated AABB half-height, sum_j |R_zj| h_j, and every
+    ground point lies on z = 0 (touching), so every row carries
+    (x_z + e_z) / 0.15; t1.x, t1.y are the ground frame's (1, 0)."""
+    hx, hy, hz = 0.0375, 0.0125, 0.0075
+    a, c = np.radians(30.0), np.radians(20.0)
+    qx = np.array([np.cos(a / 2), np.sin(a / 2), 0.0, 0.0])
+    qz = np.array([np.cos(c / 2), 0.0, 0.0, np.sin(c / 2)])
+    w0, x0, y0, z0 = qz
+    w1, x1, y1, z1 = qx
+    q = np.array([w0 * w1 - x0 * x1 - y0 * y1 - z0 * z1, w0 * x1 + x0 * w1 + y0 * z1 - z0 * y1,
+                  w0 * y1 - x0 * z1 + y0 * w1 + z0 * x1, w0 * z1 + x0 * y1 - y0 * x1 + z0 * w1])   # qz (x) qx
+    R = oracle.rotmat(q)
+    ez = abs(R[2, 0]) * hx + abs(R[2, 1]) * hy + abs(R[2, 2]) * hz
+    sc = synth.custom_scene([dict(half=(hx, hy, hz), x=(0, 0, ez), q=tuple(q), mass=0.015, mu=0.4)], ground_mu=0.4)
+    for k in ("half", "x", "q", "v", "w", "mass", "mu", "ground_mu"):
+        setattr(sc, k, getattr(sc, k).astype(float))
+    sc.half[:, 0] = (hx, hy, hz); sc.x[:, 0] = (0, 0, ez); sc.q[:, 0] = q; sc.mass[:] = 0.015
+    W = oracle.World(sc, synth.params(residual_tol=1e-10, pgs_iter_cap=20000))
+    W.set_recorder(64, 1)
+    W.step(1)
+    rows = W.recorded()
+    C = oracle.contact_dicts(W.contacts(0))
+    assert len(C) == 1 and C[0]["a"] == -1 and len(rows) == C[0]["np"] >= 2   # an edge: 2 corners
+    assert np.allclose(C[0]["p"][:, 2], 0.0, atol=1e-9)
+    assert np.allclose(rows[:, 9], 2 * ez / 0.15, atol=1e-9)
+    assert np.allclose(rows[:, 7:9], [1.0, 0.0], atol=1e-12)
