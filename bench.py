@@ -206,7 +206,10 @@ def prepare_learned(args, rank, prm, device):
                              "PGS's trajectory",
                      "plain_sweeps": float(gate["plain"].sum()), "learned_sweeps": float(gate["learned"].sum()),
                      "first_step_gain": float(gate["plain"][0] / max(gate["learned"][0], 1.0)),
-                     "gain": gate["gain"], "learned_capped": gate["learned_capped"]},
+                     "gain": gate["gain"], "learned_capped": gate["learned_capped"],
+                     "plain_body_steps_per_s": gate["body_steps"] / max(gate["plain_ms"] * 1e-3, 1e-12),
+                     "learned_body_steps_per_s": gate["body_steps"] / max(gate["learned_ms"] * 1e-3, 1e-12),
+                     "learned_over_plain": gate["plain_ms"] / max(gate["learned_ms"], 1e-12)},
             "trajectories": {"episodes": args.gate_episodes, "steps": args.gate_steps,
                              "plain_sweeps_per_solve": traj["plain"]["sweeps_per_solve"],
                              "learned_sweeps_per_solve": traj["learned"]["sweeps_per_solve"],
@@ -675,7 +678,9 @@ def main():
                            if kept else "plain (previous-frame)"
                            + (": the gate rejected the network" if learned else ""),
                            "training": learned, "comparison": compare,
-                           "learned_over_plain": compare["learned_over_plain_mean"] if compare else None},
+                           "learned_over_plain": compare["learned_over_plain_mean"] if compare else None,
+                           "learned_over_plain_identical_states": (learned["gate"]["learned_over_plain"]
+                                                                   if learned else None)},
             "plain_pgs_unaccelerated": unaccel,
             "autotune": tuning,
             "roofline": roof, "fp32_probe": peak, "gpu_launches": args.steps * launches[0],

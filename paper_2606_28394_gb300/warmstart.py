@@ -223,29 +223,46 @@ def paired(scene, prot, params, net, steps, mode=2, device="cuda"):
     impulses over a stack's redundant supports are not unique, and the
     episodes are chaotic), so comparing them measures where each trajectory
     went as much as what the network saves; this pairing measures only the
-    latter.  Returns the per-step sweep sums of both arms and their totals'
-    ratio (plain / learned)."""
+    latter.  Returns the per-step sweep sums of both arms, their totals'
+    ratio (plain / learned), and the device time of each arm's step launches
+    (CUDA events on the batch stream) over the same body-steps."""
     b = Batch(scene, dict(params, warm_start=1), max_moves=int(prot.off[-1]), device=device)
     check(jb_set_warmstart_mlp(b.h, net.block.data_ptr()), "jb_set_warmstart_mlp")
     b.set_protocol(prot)
+    import torch
     plain, learned = [], []
+    ms = {"plain": 0.0, "learned": 0.0}
     capped = 0
     total = lambda: float(b.stats()["total_sweeps"].sum())
+
+    def timed_step(name):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(b.stream)
+        b.run_protocol(1)
+        e1.record(b.stream)
+        e1.synchronize()
+        ms[name] += e0.elapsed_time(e1)
+
+    body_steps = 0.0
     for _ in range(steps):
         snap = b.save_state()
         st0 = b.stats()
         s0, c0 = float(st0["total_sweeps"].sum()), int(st0["capped_solves"].sum())
+        b0 = float(st0["body_steps"].sum())
         b.set_params(dict(params, warm_start=mode))
-        b.run_protocol(1)
+        timed_step("learned")
         st = b.stats()
         learned.append(float(st["total_sweeps"].sum()) - s0)
         capped += int(st["capped_solves"].sum()) - c0
         b.load_state(snap)
         s0 = total()
         b.set_params(dict(params, warm_start=1))
-        b.run_protocol(1)
-        plain.append(total() - s0)
+        timed_step("plain")
+        st = b.stats()
+        plain.append(float(st["total_sweeps"].sum()) - s0)
+        body_steps += float(st["body_steps"].sum()) - b0
     plain, learned = np.array(plain), np.array(learned)
-    st = b.stats()
     return {"plain": plain, "learned": learned, "gain": float(plain.sum() / max(learned.sum(), 1.0)),
-            "plain_capped": int(st["capped_solves"].sum()), "learned_capped": capped}
+            "plain_capped": int(st["capped_solves"].sum()), "learned_capped": capped,
+            # the same body-steps in both arms; device time of the step launches
+            "body_steps": body_steps, "plain_ms": ms["plain"], "learned_ms": ms["learned"]}
