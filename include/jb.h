@@ -399,12 +399,14 @@ jb_status jb_set_recorder_points(jb_batch* b, int32_t unmatched_only);
 
 size_t jb_mlp_bytes(void);              /* device bytes of a network block */
 int32_t jb_mlp_param_count(void);       /* floats of one parameter set */
-/* Device scratch of jb_mlp_forward / jb_mlp_grad / jb_mlp_train_step (the
- * gradient, the loss and an error flag; the same for every n > 0; 0 for
+/* Device scratch of jb_mlp_forward / jb_mlp_grad / jb_mlp_train_step for n
+ * rows (the gradient, the loss, an error flag and one row of partial sums per
+ * CTA, up to 160 CTAs: about 80 KB per 128 rows, at most 12.8 MB; 0 for
  * n <= 0).  The batch forward and the gradient run in one fused kernel on the
  * tcgen05 tensor cores (BF16 operands in shared memory, FP32 accumulators in
  * tensor memory), one CTA per 128 rows up to one per SM; the rows and
- * activations never go to global memory. */
+ * activations never go to global memory.  The CTAs' partial sums are added
+ * in a fixed order, so the gradient is bitwise reproducible. */
 size_t jb_mlp_scratch_bytes(int32_t n);
 /* Loads parameters (host, jb_mlp_param_count floats, layout above) into the
  * block, zeroes the AdamW moments and packs the BF16 operands. */

@@ -101,7 +101,7 @@ __global__ void mlp_adamw_kernel(unsigned char* mlp, const float* __restrict__ g
 using namespace jbk;
 
 cudaError_t jbk_mlp_tc_launch(const unsigned char* mlp, const float* X, const float* T, int n, int mode, float* Y,
-                              float* grad, float* loss, int* err, cudaStream_t s);
+                              float* part, int pstride, float* grad, float* loss, int* err, cudaStream_t s);
 
 namespace {
 #define MCU(call)                                                                                    \
@@ -111,18 +111,26 @@ namespace {
   } while (0)
 
 struct Scratch {
-  float *grad, *loss;
+  float *grad, *loss, *part;
   int* err;
+  int pstride;
   size_t bytes;
 };
 
-Scratch carve_scratch(unsigned char* base) {
+// gradient, loss, error flag, and the per-CTA partial sums of the gradient
+// kernel (one row of pstride floats per CTA, min(tiles, kTcMaxGrid) rows)
+Scratch carve_scratch(unsigned char* base, int n) {
   Scratch s;
   size_t o = 0;
   auto take = [&](size_t b) { unsigned char* p = base ? base + o : nullptr; o = (o + b + 255) & ~size_t(255); return p; };
-  s.grad = (float*)take((size_t)mlp_layout().nparam * 4);
+  const int nparam = mlp_layout().nparam;
+  s.pstride = (nparam + 1 + 63) & ~63;
+  const int tiles = (n + 127) / 128;
+  const int rows = tiles < kTcMaxGrid ? tiles : kTcMaxGrid;
+  s.grad = (float*)take((size_t)nparam * 4);
   s.loss = (float*)take(4);
   s.err = (int*)take(4);
+  s.part = (float*)take((size_t)rows * s.pstride * 4);
   s.bytes = o;
   return s;
 }
@@ -134,7 +142,7 @@ extern "C" {
 
 size_t jb_mlp_bytes(void) { return (size_t)mlp_layout().bytes; }
 int32_t jb_mlp_param_count(void) { return mlp_layout().nparam; }
-size_t jb_mlp_scratch_bytes(int32_t n) { return n > 0 ? carve_scratch(nullptr).bytes : 0; }
+size_t jb_mlp_scratch_bytes(int32_t n) { return n > 0 ? carve_scratch(nullptr, n).bytes : 0; }
 
 jb_status jb_mlp_load(void* d_mlp, const float* params, void* stream) {
   if (!d_mlp || !params) return fail(JB_EINVAL, "jb_mlp_load: null argument");
@@ -162,11 +170,11 @@ jb_status jb_mlp_forward(const void* d_mlp, const float* d_x, int32_t n, float* 
   if (!d_mlp || !d_x || !d_y || n < 0) return fail(JB_EINVAL, "jb_mlp_forward: bad argument");
   if (n == 0) return JB_OK;
   if (!d_scratch || bytes < jb_mlp_scratch_bytes(n)) return fail(JB_ENOMEM, "jb_mlp_forward: scratch too small");
-  Scratch sc = carve_scratch(static_cast<unsigned char*>(d_scratch));
+  Scratch sc = carve_scratch(static_cast<unsigned char*>(d_scratch), n);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   MCU(cudaMemsetAsync(sc.err, 0, sizeof(int), s));
-  MCU(jbk_mlp_tc_launch(static_cast<const unsigned char*>(d_mlp), d_x, nullptr, n, 0, d_y, nullptr, nullptr, sc.err,
-                        s));
+  MCU(jbk_mlp_tc_launch(static_cast<const unsigned char*>(d_mlp), d_x, nullptr, n, 0, d_y, nullptr, 0, nullptr,
+                        nullptr, sc.err, s));
   return JB_OK;
 }
 
@@ -177,20 +185,17 @@ jb_status jb_mlp_grad(const void* d_mlp, const float* d_x, const float* d_t, int
                       void* d_scratch, size_t bytes, void* stream) {
   if (!d_mlp || !d_x || !d_t || !d_grad || n <= 0) return fail(JB_EINVAL, "jb_mlp_grad: bad argument");
   if (!d_scratch || bytes < jb_mlp_scratch_bytes(n)) return fail(JB_ENOMEM, "jb_mlp_grad: scratch too small");
-  const MlpLayout L = mlp_layout();
-  Scratch sc = carve_scratch(static_cast<unsigned char*>(d_scratch));
+  Scratch sc = carve_scratch(static_cast<unsigned char*>(d_scratch), n);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  MCU(cudaMemsetAsync(d_grad, 0, sizeof(float) * L.nparam, s));
-  if (d_loss) MCU(cudaMemsetAsync(d_loss, 0, sizeof(float), s));
   MCU(cudaMemsetAsync(sc.err, 0, sizeof(int), s));
-  MCU(jbk_mlp_tc_launch(static_cast<const unsigned char*>(d_mlp), d_x, d_t, n, 1, nullptr, d_grad, d_loss, sc.err,
-                        s));
+  MCU(jbk_mlp_tc_launch(static_cast<const unsigned char*>(d_mlp), d_x, d_t, n, 1, nullptr, sc.part, sc.pstride,
+                        d_grad, d_loss, sc.err, s));
   return JB_OK;
 }
 
 jb_status jb_mlp_scratch_error(const void* d_scratch, size_t bytes, void* stream, int32_t* out) {
   if (!d_scratch || !out || bytes < jb_mlp_scratch_bytes(1)) return fail(JB_EINVAL, "jb_mlp_scratch_error: bad argument");
-  Scratch sc = carve_scratch(static_cast<unsigned char*>(const_cast<void*>(d_scratch)));
+  Scratch sc = carve_scratch(static_cast<unsigned char*>(const_cast<void*>(d_scratch)), 1);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int v = 0;
   MCU(cudaMemcpyAsync(&v, sc.err, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -218,7 +223,7 @@ jb_status jb_mlp_train_step(void* d_mlp, const float* d_x, const float* d_t, int
                             size_t bytes, void* stream) {
   if (n <= 0) return fail(JB_EINVAL, "jb_mlp_train_step: n must be > 0");
   if (!d_scratch || bytes < jb_mlp_scratch_bytes(n)) return fail(JB_ENOMEM, "jb_mlp_train_step: scratch too small");
-  Scratch sc = carve_scratch(static_cast<unsigned char*>(d_scratch));
+  Scratch sc = carve_scratch(static_cast<unsigned char*>(d_scratch), n);
   if (jb_status st = jb_mlp_grad(d_mlp, d_x, d_t, n, sc.grad, d_loss, d_scratch, bytes, stream)) return st;
   return jb_mlp_adamw(d_mlp, sc.grad, step, lr, beta1, beta2, eps, weight_decay, stream);
 }

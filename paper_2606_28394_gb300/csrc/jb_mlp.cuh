@@ -38,6 +38,11 @@ __host__ __device__ inline uint32_t kmaj_off(int r, int k, int K) {
   return (uint32_t)((r >> 3) * (K * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
 }
 
+// The tensor-core kernel's gradient: at most kTcMaxGrid CTAs, each writing
+// its partial sums (parameters, then the loss) to a row of the scratch, which
+// a second kernel sums in CTA order.
+constexpr int kTcMaxGrid = 160;
+
 // Layout of the network block in device memory (FP32 unless noted).
 struct MlpLayout {
   // master weights, row-major [in][out]

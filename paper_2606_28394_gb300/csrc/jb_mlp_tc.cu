@@ -190,12 +190,13 @@ __device__ __forceinline__ bool bit(const uint32_t (&m)[4], int c) { return (m[c
 // accumulated with atomics, zeroed by the caller).
 __global__ void __launch_bounds__(kRows, 1)
     mlp_tc_kernel(const unsigned char* __restrict__ mlp, const float* __restrict__ X, const float* __restrict__ T,
-                  int n, int mode, float* __restrict__ Y, float* __restrict__ grad, float* __restrict__ loss,
+                  int n, int mode, float* __restrict__ Y, float* __restrict__ part, int pstride,
                   int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_base;
-  __shared__ float b1s[kHid], b2s[kHid], b3s[4], db3s[4], loss_s;
+  __shared__ float b1s[kHid], b2s[kHid], b3s[4];
+  __shared__ float red_s[4][4];   // per warp: the three output-bias sums and the loss
   __shared__ int bad;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const MlpLayout L = mlp_layout();
@@ -206,12 +207,9 @@ __global__ void __launch_bounds__(kRows, 1)
 
   b1s[tid] = P[L.b1 + tid];
   b2s[tid] = P[L.b2 + tid];
-  if (tid < 4) {
-    b3s[tid] = tid < kOut ? P[L.b3 + tid] : 0.f;
-    db3s[tid] = 0.f;
-  }
+  if (tid < 4) b3s[tid] = tid < kOut ? P[L.b3 + tid] : 0.f;
+  if (tid < 16) red_s[tid >> 2][tid & 3] = 0.f;
   if (tid == 0) {
-    loss_s = 0.f;
     bad = 0;
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -342,12 +340,9 @@ __global__ void __launch_bounds__(kRows, 1)
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) red[i] += __shfl_xor_sync(0xffffffffu, red[i], o);
-      if (lane == 0) {
-        atomicAdd(&db3s[0], red[0]);
-        atomicAdd(&db3s[1], red[1]);
-        atomicAdd(&db3s[2], red[2]);
-        atomicAdd(&loss_s, red[3]);
-      }
+      if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) red_s[warp][i] += red[i];
     }
     issue_begin();
     if (tid == 0) {
@@ -394,28 +389,35 @@ __global__ void __launch_bounds__(kRows, 1)
   }
 
   if (mode == 1 && bad == 0) {
-    // this thread's TMEM lane is hidden unit tid of every gradient accumulator
+    // this CTA's partial sums, in the parameter layout, at row blockIdx.x of
+    // the partials (summed over CTAs in a fixed order by the next kernel, so
+    // that the gradient is bitwise reproducible); this thread's TMEM lane is
+    // hidden unit tid of every accumulator
+    float* g = part + (size_t)blockIdx.x * pstride;
     float v[16];
     for (int c0 = 0; c0 < kHid; c0 += 16) {
       tmem_ld16(tl + kColDW2 + c0, v);
 #pragma unroll
-      for (int i = 0; i < 16; ++i) atomicAdd(grad + L.w2 + tid * kHid + c0 + i, v[i]);
+      for (int i = 0; i < 16; ++i) g[L.w2 + tid * kHid + c0 + i] = v[i];
     }
     for (int c0 = 0; c0 < 32; c0 += 16) {
       tmem_ld16(tl + kColDW1 + c0, v);
 #pragma unroll
       for (int i = 0; i < 16; ++i)
-        if (c0 + i < kFeat) atomicAdd(grad + L.w1 + (c0 + i) * kHid + tid, v[i]);
+        if (c0 + i < kFeat) g[L.w1 + (c0 + i) * kHid + tid] = v[i];
     }
     tmem_ld16(tl + kColDW3, v);
 #pragma unroll
-    for (int o = 0; o < kOut; ++o) atomicAdd(grad + L.w3 + tid * kOut + o, v[o]);
+    for (int o = 0; o < kOut; ++o) g[L.w3 + tid * kOut + o] = v[o];
     tmem_ld16(tl + kColDB1, v);
-    atomicAdd(grad + L.b1 + tid, v[0]);
+    g[L.b1 + tid] = v[0];
     tmem_ld16(tl + kColDB2, v);
-    atomicAdd(grad + L.b2 + tid, v[0]);
-    if (tid < kOut) atomicAdd(grad + L.b3 + tid, db3s[tid]);
-    if (tid == 0 && loss) atomicAdd(loss, loss_s);
+    g[L.b2 + tid] = v[0];
+    if (tid < 4) {
+      const float r = ((red_s[0][tid] + red_s[1][tid]) + red_s[2][tid]) + red_s[3][tid];
+      if (tid < kOut) g[L.b3 + tid] = r;
+      else g[L.nparam] = r;   // the loss
+    }
   }
   if (bad && tid == 0) {
     atomicExch(err, 1);
@@ -430,13 +432,28 @@ __global__ void __launch_bounds__(kRows, 1)
   }
 }
 
+// grad[i] = sum over the G CTA partials of entry i, in CTA order (entry
+// nparam is the loss).
+__global__ void mlp_partial_sum_kernel(const float* __restrict__ part, int G, int pstride, float* __restrict__ grad,
+                                       float* __restrict__ loss) {
+  const MlpLayout L = mlp_layout();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > L.nparam) return;
+  float s = 0.f;
+  for (int b = 0; b < G; ++b) s += part[(size_t)b * pstride + i];
+  if (i < L.nparam) grad[i] = s;
+  else if (loss) *loss = s;
+}
+
 }  // namespace tc
 }  // namespace jbk
 
-// Launches the fused kernel over n rows: grid = min(tiles, SMs), one CTA per
-// SM (its shared memory fills the SM).  Returns a CUDA error code.
+// Launches the fused kernel over n rows: grid = min(tiles, SMs, kTcMaxGrid),
+// one CTA per SM (its shared memory fills the SM); for the gradient, then the
+// fixed-order sum of the CTAs' partials (part holds kTcMaxGrid rows of
+// pstride floats).  Returns a CUDA error code.
 cudaError_t jbk_mlp_tc_launch(const unsigned char* mlp, const float* X, const float* T, int n, int mode, float* Y,
-                              float* grad, float* loss, int* err, cudaStream_t s) {
+                              float* part, int pstride, float* grad, float* loss, int* err, cudaStream_t s) {
   using namespace jbk::tc;
   static int configured_device = -1;
   int dev = 0;
@@ -451,8 +468,13 @@ cudaError_t jbk_mlp_tc_launch(const unsigned char* mlp, const float* X, const fl
   e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
   const int tiles = (n + kRows - 1) / kRows;
-  const int grid = tiles < nsm ? tiles : nsm;
+  int grid = tiles < nsm ? tiles : nsm;
+  if (grid > jbk::kTcMaxGrid) grid = jbk::kTcMaxGrid;
   if (grid <= 0) return cudaSuccess;
-  mlp_tc_kernel<<<grid, kRows, kSmemBytes, s>>>(mlp, X, T, n, mode, Y, grad, loss, err);
+  mlp_tc_kernel<<<grid, kRows, kSmemBytes, s>>>(mlp, X, T, n, mode, Y, part, pstride, err);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || mode != 1) return e;
+  const int nsum = jbk::mlp_layout().nparam + 1;
+  mlp_partial_sum_kernel<<<(nsum + 255) / 256, 256, 0, s>>>(part, grid, pstride, grad, loss);
   return cudaGetLastError();
 }

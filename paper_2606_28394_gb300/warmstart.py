@@ -127,7 +127,12 @@ def collect(scene, prot, params, capacity, every=1, max_steps=1 << 30, device="c
     b.run_protocol(max_steps)
     b.sync()
     n = min(int(count.item()), capacity)
-    return rows[:n]
+    rows = rows[:n]
+    # the recorder's warps claim rows in whatever order they reach them: put
+    # the rows in an order fixed by their contents (a projection on a fixed
+    # random direction, in FP64), so that everything downstream repeats
+    key = rows.double() @ torch.from_numpy(np.random.default_rng(12345).standard_normal(REC)).to(rows.device)
+    return rows[torch.argsort(key, stable=True)].contiguous()
 
 
 def train(rows, epochs=30, batch=8192, lr=3e-4, wd=1e-4, val_frac=0.2, seed=0, device="cuda", log=None):

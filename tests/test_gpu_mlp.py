@@ -207,6 +207,28 @@ def test_tensor_core_kernel_matches_a_bf16_faithful_reference(cuda_device, n):
         assert float(cos) > 0.9999
 
 
+def test_collection_and_training_are_bitwise_reproducible(cuda_device):
+    """Two runs of the same collection and training give the same rows and
+    the same parameters, bit for bit: the recorded rows are put in an order
+    fixed by their contents, and the tensor-core kernel adds its CTAs'
+    partial gradients in CTA order (more rows than one CTA takes, so several
+    CTAs contribute)."""
+    import torch
+    sc, pr, prm = synth.friction_workload(seed=3001)
+    prm = dict(prm, residual_tol=1e-5, pgs_iter_cap=20000, pgs_accel_period=64)
+    s_tr, p_tr = synth.subset(sc, pr, range(0, 450, 45))
+    runs = []
+    for _ in range(2):
+        rows = ws().collect(s_tr, p_tr, prm, capacity=200000, every=1, max_steps=60, unmatched_only=True)
+        net, hist = ws().train(rows, epochs=3, batch=2048, lr=1e-3, seed=0)
+        runs.append((rows, net.params(), hist))
+    (r0, p0, h0), (r1, p1, h1) = runs
+    assert r0.shape[0] > 4 * 128
+    assert torch.equal(r0, r1)
+    assert np.array_equal(p0, p1)
+    assert [h[1:] for h in h0] == [h[1:] for h in h1]
+
+
 def test_learned_warm_start_without_network_is_refused(cuda_device):
     scene = synth.build_scene([synth.Tower(levels=2)], 0)
     b = jb().Batch(scene, synth.params(warm_start=2))
