@@ -14,8 +14,9 @@
 // signalled through an mbarrier.  The epilogues read the accumulators back
 // with tcgen05.ld (one TMEM lane per thread), apply bias, ReLU or the ReLU
 // mask, round to BF16 and write the next operands to shared memory.  The
-// weight-gradient accumulators stay in TMEM across the CTA's tiles and are
-// added to the FP32 gradient with atomics once at the end.
+// weight-gradient accumulators stay in TMEM across the CTA's tiles; at the
+// end each CTA writes them as one row of partial sums, and a second kernel
+// adds the rows in CTA order, so the gradient repeats bit for bit.
 //
 // Operands live in shared memory in the K-major layout without swizzle:
 // 8 x 8 BF16 core matrices (8 rows of 16 bytes, contiguous), the core
