@@ -157,8 +157,8 @@ MLP_FLOP = 2.0 * (24 * 128 + 128 * 128 + 128 * 3)   # per predicted contact poin
 #  -k regex:episode_kernel -s 3 -c 1 python bench.py --warm-start plain --no-cpu --no-compare
 #  --episodes 45 --max-steps 300 --steps 1 --warmup 3` (1 pass).  Valid only for
 # the kernel sources it was taken on; any change to them reports null.
-TRAFFIC = {"bytes_per_body_step": (1917952.0 + 4678656.0) / 720900.0, "case": "45 episodes x 300 steps",
-           "workload": "friction", "sources_sha1": "d6650bff42ede7ec7c3a27aa7ccf7ed0260ff83c"}
+TRAFFIC = {"bytes_per_body_step": (1827072.0 + 4494336.0) / 720900.0, "case": "45 episodes x 300 steps",
+           "workload": "friction", "sources_sha1": "aa1b20f3193efea79f4f102c42c73221450e6143"}
 
 
 def kernel_sources_sha1():
